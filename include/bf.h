@@ -1,0 +1,171 @@
+/*
+ * bf.h -- C ABI of libbf, a GB300 (sm_103a) implementation of the Monte Carlo
+ * shiftable bilateral filter for vector-valued images (Ghosh & Chaudhury,
+ * "Fast Bilateral Filtering of Vector-Valued Images", arXiv 1605.02164).
+ *
+ * The filter (Eqs. BF, normal) is
+ *     B[f](i) = sum_j w(j) phi(f(i-j) - f(i)) f(i-j) / sum_j w(j) phi(f(i-j) - f(i)),
+ *     w(j) = exp(-|j|^2 / (2 sigma_s^2)),  phi(x) = exp(-x^T C^{-1} x / 2),
+ * over the window |j_x|, |j_y| <= r = floor(3 sigma_s) (Section 1), leaving out
+ * neighbours outside the image.  libbf computes the paper's approximation
+ * (Algorithm 1, Eqs. numerator and denom): the range kernel is whitened, each
+ * 1-D Gaussian is replaced by a raised cosine of order N (Eq. approx), and the
+ * product of raised cosines is sampled with K = T Monte Carlo draws
+ * (Prop. 2, Eq. finalApproxY).  With nu_t = W^T Y_t / (2 pi sqrt(N)) the output is
+ *     S_c(i) = Re P_c(i) / Re Z(i),
+ *     P_c(i) = sum_t sum_j w(j) cos(2 pi nu_t . (f(i-j) - f(i))) f_c(i-j),
+ *     Z(i)   = sum_t sum_j w(j) cos(2 pi nu_t . (f(i-j) - f(i))),
+ * evaluated in shiftable form: per term, 2(d+1) modulated channels
+ * (cos th f_c, sin th f_c, cos th, sin th) are blurred by the Gaussian and
+ * combined with the centre pixel's cos th and sin th.
+ *
+ * Conventions for every call:
+ *   - Return value: BF_OK (0) on success, else one negative BF_ERR_* code.
+ *     Nothing is written to outputs on a host-side error.
+ *   - Images are FP32, planar [d][H][pitch] (element (c, y, x) at
+ *     base[c*H*pitch + y*pitch + x]), on the device unless the call says host.
+ *     The caller owns image buffers and streams; libbf owns plans and its
+ *     internal scratch.
+ *   - Filtering calls are asynchronous on the given stream (NULL = legacy
+ *     default stream) and launch only CUDA kernels of this library; there is
+ *     no CPU fallback.  Input and output must not overlap (no in-place).
+ *   - A stream argument is a cudaStream_t passed as void*.
+ */
+#ifndef BF_H_
+#define BF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define BF_OK 0
+#define BF_ERR_ARG (-1)         /* null pointer, bad size, overlap, bad enum */
+#define BF_ERR_NOT_SPD (-2)     /* C is not symmetric positive definite */
+#define BF_ERR_D_RANGE (-3)     /* d outside [1, BF_MAX_D] */
+#define BF_ERR_ALIGN (-4)       /* pointer or pitch misaligned */
+#define BF_ERR_NOMEM (-5)       /* device or host allocation failed */
+#define BF_ERR_BUDGET (-6)      /* request exceeds a memory budget */
+#define BF_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
+#define BF_ERR_CUDA (-8)        /* a CUDA runtime call failed */
+#define BF_ERR_UNSUPPORTED (-9) /* parameters outside what the kernels handle */
+
+#define BF_MAX_D 8        /* channels per pixel */
+#define BF_MAX_RADIUS 32  /* window half-width r (sigma_s up to 10.99) */
+#define BF_MAX_N 4096     /* raised-cosine order */
+#define BF_MAX_K 65536    /* Monte Carlo terms */
+
+/* Kernel variants of the blur step. */
+#define BF_FP32 0   /* every step in FP32 on the CUDA cores */
+#define BF_FP16TC 1 /* modulated channels in FP16, blur on tensor cores, FP32 accumulation */
+#define BF_BF16TC 2 /* as BF_FP16TC with BF16 channels */
+
+/* Whitening of the range kernel (Eq. COB). */
+#define BF_WHITEN_CHOLESKY 0 /* W = L^{-1}, C = L L^T */
+#define BF_WHITEN_EIGEN 1    /* W = diag(alpha) Q^T, C^{-1} = Q diag(alpha^2) Q^T (the paper's) */
+
+typedef struct bf_plan_s *bf_plan_t; /* opaque; owned by the library */
+
+/*
+ * bf_plan -- build the sampled frequency list for (d, C, sigma_s, N, K, seed).
+ * Follows Algorithm 1's set-up (diagonalise/whiten C, set up the spatial
+ * filter, gamma = 1/sqrt(N)) and its "Draw X from B(N,1/2)^d" step, done once
+ * for all K terms (Prop. 2, Eq. finalApproxY).
+ *   d        channels, 1..BF_MAX_D (else BF_ERR_D_RANGE).
+ *   C        host pointer, d*d doubles, row-major; symmetric positive definite
+ *            (else BF_ERR_NOT_SPD; asymmetry beyond 1e-9 relative is BF_ERR_ARG).
+ *   sigma_s  spatial standard deviation > 0; r = floor(3 sigma_s) must be
+ *            <= BF_MAX_RADIUS (else BF_ERR_UNSUPPORTED).
+ *   N        raised-cosine order, 1..BF_MAX_N; 0 selects 10, the order used
+ *            in all of the paper's experiments.
+ *   K        Monte Carlo terms (the paper's T), 1..BF_MAX_K.
+ *   seed     64-bit seed of the counter-based SplitMix64 stream: X_tk is the
+ *            number of ones among N bits taken from ceil(N/64) consecutive
+ *            outputs, t-major then k.
+ *   out      receives the plan handle.
+ * The whitening and the frequency vectors nu_t are computed on the device in
+ * FP64 (Cholesky factor of C and back substitution); the call returns after
+ * that kernel has finished.  The plan's device memory stays resident until
+ * bf_plan_destroy.  Thread-safe; uses its own stream internally.
+ */
+int bf_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t seed, bf_plan_t *out);
+
+/* As bf_plan, with the whitening chosen by `whiten` (BF_WHITEN_*) and the
+ * window half-width forced to `radius` when radius >= 0 (radius < 0 keeps
+ * floor(3 sigma_s)). */
+int bf_plan_ex(int d, const double *C, double sigma_s, int N, int K, uint64_t seed, int whiten, int radius,
+               bf_plan_t *out);
+
+/* Copy the plan's frequency list to host memory: nu_host (may be NULL) gets
+ * K*d doubles, nu_t in turns (omega_t / 2 pi), row t = term; Y_host (may be
+ * NULL) gets the K*d sampled integers Y_t = N - 2 X_t. */
+int bf_plan_get_freqs(bf_plan_t plan, double *nu_host, int32_t *Y_host);
+
+/* Plan parameters; any output pointer may be NULL. */
+int bf_plan_info(bf_plan_t plan, int *d, int *K, int *N, int *radius, double *sigma_s);
+
+/* Release the plan's device memory.  The caller must ensure no filtering call
+ * that uses the plan is still in flight. */
+int bf_plan_destroy(bf_plan_t plan);
+
+/*
+ * bf_filter -- apply the plan to one image (Algorithm 1's loop over t and the
+ * final division), asynchronously on `stream`.
+ *   in, out  device pointers, planar [d][H][pitch] FP32, 16-byte aligned
+ *            (else BF_ERR_ALIGN); out receives S_c = Re P_c / Re Z for every
+ *            pixel; padding columns x >= W of out are not written.
+ *   H, W     image size; H == 0 or W == 0 is a no-op returning BF_OK.
+ *   pitch    row stride in elements, pitch >= W and pitch % 4 == 0.
+ *   variant  BF_FP32, BF_FP16TC or BF_BF16TC.
+ * Pixels whose Re Z is exactly 0 come out as IEEE inf/nan; nothing is clamped.
+ */
+int bf_filter(bf_plan_t plan, const float *in, float *out, int H, int W, int pitch, int variant, void *stream);
+
+/* One image of a batch. */
+typedef struct {
+    bf_plan_t plan;
+    const float *in; /* device, planar [d][H][pitch] */
+    float *out;      /* device, planar [d][H][pitch] */
+    int H, W, pitch;
+} bf_item;
+
+/*
+ * bf_filter_batch -- filter n independent images (each with its own plan,
+ * size, d, sigma_s and K) in one persistent-kernel launch that pops tiles of
+ * all images from a device work queue.  Same rules per item as bf_filter.
+ * Results equal those of n separate bf_filter calls with the same variant.
+ * `items` is a host array; it is copied before the call returns.
+ */
+int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
+
+/*
+ * bf_filter_host -- end-to-end convenience call for callers holding host
+ * images: copies `in_host` (planar [d][H][W], pitch W) to library-owned
+ * device buffers, filters, copies the result to `out_host`, and synchronises
+ * `stream` before returning.  Host buffers may be pageable; pinned buffers
+ * give overlapped copies.  The device buffers are cached per library and
+ * grown on demand (BF_ERR_NOMEM if that fails).  Not re-entrant on the same
+ * stream from several host threads.
+ */
+int bf_filter_host(bf_plan_t plan, const float *in_host, float *out_host, int H, int W, int variant,
+                   void *stream);
+
+/* Status word of the library's device-side guards (bounded waits, tile-queue
+ * consistency) for work issued on `stream`; synchronises the stream, returns
+ * BF_OK or the first BF_ERR_* recorded, and clears it. */
+int bf_last_status(void *stream);
+
+/* Static description of an error code. */
+const char *bf_error_string(int code);
+
+/* Library version, e.g. 10000 for 1.0.0. */
+int bf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_H_ */

@@ -1,0 +1,155 @@
+// C ABI entry points: argument checks and dispatch to the fused kernels.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <mutex>
+#include <vector>
+
+#include "bf_internal.cuh"
+
+namespace bf {
+
+namespace {
+std::mutex g_status_mu;
+int *g_status[64] = {nullptr};
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+int check_image_args(const bf_plan_s *p, const float *in, const float *out, int H, int W, int pitch) {
+    if (!p) return BF_ERR_ARG;
+    if (H < 0 || W < 0) return BF_ERR_ARG;
+    if (H == 0 || W == 0) return BF_OK;
+    if (!in || !out) return BF_ERR_ARG;
+    if (pitch < W) return BF_ERR_ARG;
+    if ((pitch & 3) != 0 || !aligned16(in) || !aligned16(out)) return BF_ERR_ALIGN;
+    const size_t bytes = (size_t)p->d * H * (size_t)pitch * sizeof(float);
+    const char *a = (const char *)in, *b = (const char *)out;
+    if (a < b + bytes && b < a + bytes) return BF_ERR_ARG;  // overlap
+    return BF_OK;
+}
+}  // namespace
+
+int *status_word(int device) {
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_status_mu);
+    if (!g_status[device]) {
+        int *w = nullptr;
+        if (cudaMalloc(&w, sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cudaMemset(w, 0, sizeof(int));
+        g_status[device] = w;
+    }
+    return g_status[device];
+}
+
+}  // namespace bf
+
+extern "C" int bf_filter(bf_plan_t p, const float *in, float *out, int H, int W, int pitch, int variant,
+                         void *stream) {
+    int rc = bf::check_image_args(p, in, out, H, W, pitch);
+    if (rc != BF_OK || H == 0 || W == 0) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (variant) {
+        case BF_FP32: return bf::launch_fp32(*p, in, out, H, W, pitch, s);
+        case BF_FP16TC:
+        case BF_BF16TC: return bf::launch_tc(*p, in, out, H, W, pitch, variant, s);
+        default: return BF_ERR_ARG;
+    }
+}
+
+extern "C" int bf_filter_batch(const bf_item *items, int n, int variant, void *stream) {
+    if (n < 0 || (n > 0 && !items)) return BF_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        int rc = bf::check_image_args(items[i].plan, items[i].in, items[i].out, items[i].H, items[i].W,
+                                      items[i].pitch);
+        if (rc != BF_OK) return rc;
+    }
+    for (int i = 0; i < n; ++i) {
+        const bf_item &it = items[i];
+        if (it.H == 0 || it.W == 0) continue;
+        int rc = bf_filter(it.plan, it.in, it.out, it.H, it.W, it.pitch, variant, stream);
+        if (rc != BF_OK) return rc;
+    }
+    return BF_OK;
+}
+
+namespace {
+struct HostBuffers {
+    std::mutex mu;
+    float *dev = nullptr;
+    size_t bytes = 0;
+};
+HostBuffers g_host;
+}  // namespace
+
+extern "C" int bf_filter_host(bf_plan_t p, const float *in_host, float *out_host, int H, int W, int variant,
+                              void *stream) {
+    if (!p || H < 0 || W < 0) return BF_ERR_ARG;
+    if (H == 0 || W == 0) return BF_OK;
+    if (!in_host || !out_host) return BF_ERR_ARG;
+    const int pitch = (W + 3) & ~3;
+    const size_t img = (size_t)p->d * H * (size_t)pitch * sizeof(float);
+    const size_t need = 2 * ((img + 255) / 256 * 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    std::lock_guard<std::mutex> lk(g_host.mu);
+    if (g_host.bytes < need) {
+        if (g_host.dev) {
+            cudaStreamSynchronize(s);
+            cudaFree(g_host.dev);
+        }
+        g_host.dev = nullptr;
+        g_host.bytes = 0;
+        if (cudaMalloc(&g_host.dev, need) != cudaSuccess) {
+            cudaGetLastError();
+            return BF_ERR_NOMEM;
+        }
+        g_host.bytes = need;
+    }
+    float *din = g_host.dev;
+    float *dout = (float *)((char *)g_host.dev + need / 2);
+    const size_t plane_h = (size_t)H * W, plane_d = (size_t)H * pitch;
+    int rc = BF_OK;
+    for (int c = 0; c < p->d && rc == BF_OK; ++c)
+        rc = bf::cuda_err(cudaMemcpy2DAsync(din + c * plane_d, pitch * sizeof(float), in_host + c * plane_h,
+                                            W * sizeof(float), W * sizeof(float), H, cudaMemcpyHostToDevice, s));
+    if (rc == BF_OK) rc = bf_filter(p, din, dout, H, W, pitch, variant, stream);
+    for (int c = 0; c < p->d && rc == BF_OK; ++c)
+        rc = bf::cuda_err(cudaMemcpy2DAsync(out_host + c * plane_h, W * sizeof(float), dout + c * plane_d,
+                                            pitch * sizeof(float), W * sizeof(float), H, cudaMemcpyDeviceToHost, s));
+    if (rc == BF_OK) rc = bf::cuda_err(cudaStreamSynchronize(s));
+    return rc;
+}
+
+extern "C" int bf_last_status(void *stream) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BF_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BF_ERR_CUDA;
+    int *w = bf::status_word(dev);
+    if (!w) return BF_ERR_NOMEM;
+    int v = 0;
+    if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BF_ERR_CUDA;
+    if (v != 0) cudaMemset(w, 0, sizeof(int));
+    return v;
+}
+
+extern "C" const char *bf_error_string(int code) {
+    switch (code) {
+        case BF_OK: return "ok";
+        case BF_ERR_ARG: return "invalid argument";
+        case BF_ERR_NOT_SPD: return "covariance is not symmetric positive definite";
+        case BF_ERR_D_RANGE: return "channel count outside [1, BF_MAX_D]";
+        case BF_ERR_ALIGN: return "pointer or pitch not 16-byte aligned";
+        case BF_ERR_NOMEM: return "allocation failed";
+        case BF_ERR_BUDGET: return "request exceeds the memory budget";
+        case BF_ERR_TIMEOUT: return "bounded device wait ran out";
+        case BF_ERR_CUDA: return "CUDA runtime error";
+        case BF_ERR_UNSUPPORTED: return "parameters outside the supported range";
+        default: return "unknown error";
+    }
+}
+
+extern "C" int bf_version(void) { return 10000; }

@@ -1,0 +1,277 @@
+// Fused FP32 kernel for the Monte Carlo shiftable bilateral filter
+// (Algorithm 1; Eqs. Ht, numerator, denom), every step on the CUDA cores.
+//
+// One CTA owns a tile of kBX x BY output pixels and keeps, across all K
+// terms, its accumulators P_1..P_d, Z in shared memory.  For each term it
+// streams the tile's input region (tile plus an r-pixel halo) down in chunks
+// of kRC rows:
+//   A  phase theta = 2 pi nu_t . f (FP32 with an exact product residual and
+//      explicit range reduction), cos/sin once per pixel, and the 2(d+1)
+//      modulated channels cos th f_c, cos th, sin th f_c, sin th  (zero
+//      outside the image: neighbours outside Omega drop out of both sums);
+//   B  horizontal Gaussian pass of the chunk into a ring of row results;
+//   C  vertical pass over the ring for the output rows that became complete,
+//      combined with the centre pixel's cos/sin:  P_c += cos th(i) Bc_c(i) +
+//      sin th(i) Bs_c(i),  Z += cos th(i) Bc(i) + sin th(i) Bs(i).
+// After the last term out_c = P_c / Z (the 1/K factors cancel).
+// Both passes are register-blocked: a thread produces 8 consecutive outputs
+// from a sliding 16-value register window, 8 taps per step (taps past 2r are
+// zero).  HBM sees the input once per term through L2 and the output once.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "bf_internal.cuh"
+
+namespace bf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRC = 16;  // region rows per chunk
+constexpr int kBX = 32;  // output columns per tile
+
+struct Geom {
+    int r, BY, RX, U8, TP, RXP, RING, RING_CS, lag, NJ, HB_SLOT;
+    size_t smem_floats;
+};
+
+__host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+template <int D>
+Geom make_geom(int r, int BY) {
+    Geom g;
+    constexpr int NCH = 2 * (D + 1);
+    g.r = r;
+    g.BY = BY;
+    g.RX = kBX + 2 * r;
+    g.U8 = cdiv(2 * r + 1, 8);
+    g.TP = 8 * g.U8;
+    g.RXP = kBX + 8 * g.U8 + 4;  // covers every column the sliding window reads; %32 == 4 spreads banks
+    g.lag = cdiv(2 * r, kRC);
+    g.RING = kRC * (g.lag + 1);
+    g.RING_CS = g.RING + kRC;
+    g.NJ = cdiv(BY + 2 * r, kRC);
+    g.HB_SLOT = NCH * kBX + 4;
+    g.smem_floats = (size_t)g.TP + (size_t)NCH * kRC * g.RXP + (size_t)g.RING * g.HB_SLOT +
+                    (size_t)g.RING_CS * kBX * 2 + (size_t)(D + 1) * BY * kBX;
+    return g;
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads, 1)
+    mcsf_fp32_kernel(const float *__restrict__ in, float *__restrict__ out, int H, int W, int pitch,
+                     const float *__restrict__ nu_hi, const float *__restrict__ nu_lo, int K,
+                     const float *__restrict__ taps_g, Geom g) {
+    constexpr int NCH = 2 * (D + 1);
+    extern __shared__ __align__(16) float smem[];
+    float *taps = smem;                                   // [TP]
+    float *CH = taps + g.TP;                              // [NCH][kRC][RXP]
+    float *HB = CH + (size_t)NCH * kRC * g.RXP;           // [RING][HB_SLOT] (= [NCH][kBX] + pad)
+    float2 *CS = reinterpret_cast<float2 *>(HB + (size_t)g.RING * g.HB_SLOT);  // [RING_CS][kBX]
+    float *ACC = reinterpret_cast<float *>(CS + (size_t)g.RING_CS * kBX);      // [D+1][BY][kBX]
+
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int r = g.r, BY = g.BY;
+    const int tx0 = blockIdx.x * kBX, ty0 = blockIdx.y * BY;
+    const size_t plane = (size_t)H * pitch;
+
+    for (int i = tid; i < g.TP; i += kThreads) taps[i] = taps_g[i];
+    for (int i = tid; i < g.RING * g.HB_SLOT; i += kThreads) HB[i] = 0.f;
+    for (int i = tid; i < (D + 1) * BY * kBX; i += kThreads) ACC[i] = 0.f;
+    __syncthreads();
+
+    for (int k = 0; k < K; ++k) {
+        float nh[D], nl[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) {
+            nh[c] = __ldg(nu_hi + k * D + c);
+            nl[c] = __ldg(nu_lo + k * D + c);
+        }
+        for (int j = 0; j < g.NJ; ++j) {
+            // ---------------- A: phases, cos/sin, modulated channels ----------
+            const int ring0 = (j * kRC) % g.RING;
+            const int cs0 = (j * kRC) % g.RING_CS;
+            for (int row = warp; row < kRC; row += kThreads / 32) {
+                const int ry = j * kRC + row;
+                const int gy = ty0 - r + ry;
+                const bool rowok = ry < BY + 2 * r && gy >= 0 && gy < H;
+                for (int col = lane; col < g.RXP; col += 32) {
+                    const int gx = tx0 - r + col;
+                    float cth = 0.f, sth = 0.f, fv[D];
+#pragma unroll
+                    for (int c = 0; c < D; ++c) fv[c] = 0.f;
+                    if (rowok && col < g.RX && gx >= 0 && gx < W) {
+                        const float *px = in + (size_t)gy * pitch + gx;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) fv[c] = __ldg(px + c * plane);
+                        // t = nu . f mod 1, with the FP32 product residual kept
+                        float tf = 0.f, te = 0.f;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) {
+                            const float p = __fmul_rn(nh[c], fv[c]);
+                            const float e = fmaf(nh[c], fv[c], -p);        // exact: nh*f - p
+                            tf = __fadd_rn(tf, __fsub_rn(p, rintf(p)));    // |.| <= 1
+                            tf = __fsub_rn(tf, rintf(tf));                 // back to [-1/2, 1/2]
+                            te = fmaf(nl[c], fv[c], __fadd_rn(te, e));
+                        }
+                        sincospif(2.f * __fadd_rn(tf, te), &sth, &cth);
+                    }
+                    float *dst = CH + row * g.RXP + col;
+#pragma unroll
+                    for (int c = 0; c < D; ++c) {
+                        dst[(size_t)c * kRC * g.RXP] = cth * fv[c];
+                        dst[(size_t)(D + 1 + c) * kRC * g.RXP] = sth * fv[c];
+                    }
+                    dst[(size_t)D * kRC * g.RXP] = cth;
+                    dst[(size_t)(2 * D + 1) * kRC * g.RXP] = sth;
+                    const int cx = col - r;
+                    if (cx >= 0 && cx < kBX) CS[(cs0 + row) * kBX + cx] = make_float2(cth, sth);
+                }
+            }
+            __syncthreads();
+            // ---------------- B: horizontal pass into the ring ---------------
+            for (int task = tid; task < kRC * NCH * (kBX / 8); task += kThreads) {
+                const int xb = task & 3;
+                const int row = (task >> 2) & (kRC - 1);
+                const int ch = task >> 6;
+                const float *src = CH + ((size_t)ch * kRC + row) * g.RXP + xb * 8;
+                float acc[8], win[16];
+#pragma unroll
+                for (int m = 0; m < 8; ++m) acc[m] = 0.f;
+                *reinterpret_cast<float4 *>(&win[0]) = *reinterpret_cast<const float4 *>(src);
+                *reinterpret_cast<float4 *>(&win[4]) = *reinterpret_cast<const float4 *>(src + 4);
+                for (int u0 = 0; u0 < g.TP; u0 += 8) {
+                    *reinterpret_cast<float4 *>(&win[8]) = *reinterpret_cast<const float4 *>(src + u0 + 8);
+                    *reinterpret_cast<float4 *>(&win[12]) = *reinterpret_cast<const float4 *>(src + u0 + 12);
+                    const float4 ta = *reinterpret_cast<const float4 *>(taps + u0);
+                    const float4 tb = *reinterpret_cast<const float4 *>(taps + u0 + 4);
+                    const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+#pragma unroll
+                    for (int uu = 0; uu < 8; ++uu)
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) acc[m] = fmaf(tv[uu], win[m + uu], acc[m]);
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) win[m] = win[m + 8];
+                }
+                float *dst = HB + (size_t)(ring0 + row) * g.HB_SLOT + ch * kBX + xb * 8;
+                *reinterpret_cast<float4 *>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                *reinterpret_cast<float4 *>(dst + 4) = make_float4(acc[4], acc[5], acc[6], acc[7]);
+            }
+            __syncthreads();
+            // ---------------- C: vertical pass + combine ----------------------
+            const int oc = j - g.lag;
+            if (oc >= 0 && oc * kRC < BY) {
+                for (int task = tid; task < kBX * (D + 1) * 2; task += kThreads) {
+                    const int x = task & 31;
+                    const int rb = (task >> 5) & 1;
+                    const int p = task >> 6;
+                    const int o0 = oc * kRC + rb * 8;
+                    const float *hc = HB + p * kBX + x;            // cos-group channel p
+                    const float *hs = HB + (D + 1 + p) * kBX + x;  // sin-group channel p
+                    float vc[8], vs[8], wc[16], ws[16];
+                    int blk = o0 % g.RING;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        vc[m] = 0.f;
+                        vs[m] = 0.f;
+                        wc[m] = hc[(size_t)(blk + m) * g.HB_SLOT];
+                        ws[m] = hs[(size_t)(blk + m) * g.HB_SLOT];
+                    }
+                    for (int v0 = 0; v0 < g.TP; v0 += 8) {
+                        blk += 8;
+                        if (blk >= g.RING) blk -= g.RING;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            wc[8 + m] = hc[(size_t)(blk + m) * g.HB_SLOT];
+                            ws[8 + m] = hs[(size_t)(blk + m) * g.HB_SLOT];
+                        }
+                        const float4 ta = *reinterpret_cast<const float4 *>(taps + v0);
+                        const float4 tb = *reinterpret_cast<const float4 *>(taps + v0 + 4);
+                        const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+#pragma unroll
+                        for (int vv = 0; vv < 8; ++vv)
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) {
+                                vc[m] = fmaf(tv[vv], wc[m + vv], vc[m]);
+                                vs[m] = fmaf(tv[vv], ws[m + vv], vs[m]);
+                            }
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            wc[m] = wc[m + 8];
+                            ws[m] = ws[m + 8];
+                        }
+                    }
+                    int crow = (o0 + r) % g.RING_CS;
+                    float *acc = ACC + ((size_t)p * BY + o0) * kBX + x;
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) {
+                        const float2 cs = CS[crow * kBX + x];
+                        acc[m * kBX] += fmaf(cs.x, vc[m], cs.y * vs[m]);
+                        if (++crow == g.RING_CS) crow = 0;
+                    }
+                }
+            }
+            // no barrier here: the next chunk's A writes CH (read only by B)
+            // and CS slots that C does not read (RING_CS has one spare chunk);
+            // the barrier after that A orders this C before the next B.
+        }
+        __syncthreads();  // term boundary: CS/HB slots are reused from row 0
+    }
+    // ---------------- divide and store -----------------------------------------
+    for (int idx = tid; idx < BY * kBX; idx += kThreads) {
+        const int y = idx / kBX, x = idx % kBX;
+        const int gy = ty0 + y, gx = tx0 + x;
+        if (gy < H && gx < W) {
+            const float z = ACC[((size_t)D * BY + y) * kBX + x];
+#pragma unroll
+            for (int c = 0; c < D; ++c)
+                out[c * plane + (size_t)gy * pitch + gx] = ACC[((size_t)c * BY + y) * kBX + x] / z;
+        }
+    }
+}
+
+template <int D>
+int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s) {
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // tallest tile (multiple of kRC, at most 128 rows) whose buffers fit
+    int BY = 128;
+    Geom g = make_geom<D>(p.r, BY);
+    while (BY > kRC && g.smem_floats * sizeof(float) > (size_t)max_smem) {
+        BY -= kRC;
+        g = make_geom<D>(p.r, BY);
+    }
+    if (BY > H) {  // short image: no taller than needed
+        int by = kRC * cdiv(H, kRC);
+        if (by < BY) {
+            BY = by;
+            g = make_geom<D>(p.r, BY);
+        }
+    }
+    const size_t bytes = g.smem_floats * sizeof(float);
+    if (bytes > (size_t)max_smem) return BF_ERR_UNSUPPORTED;
+    cudaError_t e = cudaFuncSetAttribute(mcsf_fp32_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return BF_ERR_CUDA;
+    dim3 grid(cdiv(W, kBX), cdiv(H, BY));
+    mcsf_fp32_kernel<D><<<grid, kThreads, bytes, s>>>(in, out, H, W, pitch, p.nu_hi, p.nu_lo, p.K, p.taps, g);
+    return cuda_err(cudaGetLastError());
+}
+
+}  // namespace
+
+int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s) {
+    switch (p.d) {
+        case 1: return launch_d<1>(p, in, out, H, W, pitch, s);
+        case 2: return launch_d<2>(p, in, out, H, W, pitch, s);
+        case 3: return launch_d<3>(p, in, out, H, W, pitch, s);
+        case 4: return launch_d<4>(p, in, out, H, W, pitch, s);
+        case 5: return launch_d<5>(p, in, out, H, W, pitch, s);
+        case 6: return launch_d<6>(p, in, out, H, W, pitch, s);
+        case 7: return launch_d<7>(p, in, out, H, W, pitch, s);
+        case 8: return launch_d<8>(p, in, out, H, W, pitch, s);
+        default: return BF_ERR_D_RANGE;
+    }
+}
+
+}  // namespace bf

@@ -1,0 +1,48 @@
+// Internal declarations shared by the libbf translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <vector>
+
+#include "bf.h"
+
+struct bf_plan_s {
+    int d = 0, K = 0, N = 0, r = 0, whiten = 0;
+    double sigma_s = 0.0;
+    uint64_t seed = 0;
+    int device = 0;
+    // device arrays (one allocation, `block`)
+    void *block = nullptr;
+    float *nu_hi = nullptr;    // K*d: leading FP32 part of nu_t (turns)
+    float *nu_lo = nullptr;    // K*d: FP32 remainder, nu = hi + lo to ~2^-48 relative
+    double *nu64 = nullptr;    // K*d: FP64 nu_t
+    int32_t *Y = nullptr;      // K*d
+    float *taps = nullptr;     // taps_len floats: normalised 1-D Gaussian w(u - r), zero padded
+    uint16_t *taps16 = nullptr;  // FP16 copy of the taps (tensor-core variant), taps_len
+    uint16_t *tapsbf = nullptr;  // BF16 copy of the taps, taps_len
+    int taps_len = 0;
+    // host copies
+    std::vector<int32_t> Y_host;
+    std::vector<double> nu_host;
+};
+
+namespace bf {
+
+constexpr uint32_t kPlanMagic = 0xBF1605u;
+
+// Status word: one per device, written by device guards, read by bf_last_status.
+int *status_word(int device);
+
+// FP32 fused kernel (csrc/bf_fp32.cu).
+int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s);
+
+// Tensor-core fused kernel (csrc/bf_tc.cu); variant BF_FP16TC or BF_BF16TC.
+int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int variant,
+              cudaStream_t s);
+
+inline int cuda_err(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_ERR_CUDA; }
+
+}  // namespace bf

@@ -1,0 +1,66 @@
+"""CPU-only checks of the C ABI: the library builds, loads, and exports every
+function include/bf.h declares; argument checks that return before any CUDA
+call behave as documented.  No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bf.h")
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(bf_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1605_02164_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for n in ["bf_plan", "bf_plan_ex", "bf_plan_get_freqs", "bf_plan_info", "bf_plan_destroy", "bf_filter",
+              "bf_filter_batch", "bf_filter_host", "bf_last_status", "bf_error_string", "bf_version"]:
+        assert n in names, n
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for n in _declared_functions():
+        assert hasattr(lib, n), f"{n} declared in bf.h but not exported"
+
+
+def test_error_strings_and_version(lib):
+    lib.bf_error_string.restype = ctypes.c_char_p
+    for code in range(0, -10, -1):
+        s = lib.bf_error_string(code)
+        assert s and s != b"unknown error"
+    assert lib.bf_version() >= 10000
+
+
+def test_host_side_argument_checks(lib):
+    """These return before the library touches the GPU."""
+    from paper_1605_02164_gb300 import bf
+    L = bf.lib()
+    h = ctypes.c_void_p()
+    C = (ctypes.c_double * 1)(100.0)
+    assert L.bf_plan(0, C, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_D_RANGE
+    assert L.bf_plan(9, C, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_D_RANGE
+    assert L.bf_plan(1, C, -1.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
+    assert L.bf_plan(1, C, 2.0, 10, 0, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
+    assert L.bf_plan(1, C, 2.0, 5000, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
+    assert L.bf_plan(1, C, 20.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_UNSUPPORTED
+    asym = (ctypes.c_double * 4)(100.0, 1.0, 2.0, 100.0)
+    assert L.bf_plan(2, asym, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
+    assert L.bf_plan(1, None, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
+    assert L.bf_filter(None, None, None, 4, 4, 4, 0, None) == bf.BF_ERR_ARG
+    assert L.bf_plan_destroy(None) == bf.BF_ERR_ARG
+    assert L.bf_filter_batch(None, -1, 0, None) == bf.BF_ERR_ARG
+    assert L.bf_filter_batch(None, 0, 0, None) == bf.BF_OK
