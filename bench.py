@@ -314,8 +314,8 @@ def main():
     ap.add_argument("--variant", default="fp32", choices=["fp32", "fp16tc", "bf16tc"])
     ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--seed", type=int, default=3000)
-    ap.add_argument("--cpu-crop", type=int, default=384)
-    ap.add_argument("--ref-crop", type=int, default=128)
+    ap.add_argument("--cpu-crop", type=int, default=1536)
+    ap.add_argument("--ref-crop", type=int, default=512)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     ap.add_argument("--no-cpu-baseline", action="store_true")
