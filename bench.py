@@ -104,6 +104,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_max(x: float, dist=None, device: str = "cuda") -> float:
+    """Max of a per-rank scalar over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpx(world_size: int, steps: int, pixels_per_step: int, max_seconds: float) -> float:
+    """Weak scaling: every rank filters its own images; the job's throughput is
+    all ranks' pixels over the slowest rank's time."""
+    return world_size * steps * pixels_per_step / max_seconds / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -205,14 +221,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    total_ms = t_start.elapsed_time(t_end)
+    total_ms = reduce_max(t_start.elapsed_time(t_end), dist)
     per_step = [a.elapsed_time(b) for a, b in evs]
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
     pixels = w.H * w.W
-    value = ws * args.steps * pixels / (total_ms / 1e3) / 1e6
+    value = whole_job_mpx(ws, args.steps, pixels, total_ms / 1e3)
     kernel_ms = statistics.mean(per_step)
 
     # ---- end to end through the host-buffer entry point ----------------------
@@ -226,12 +238,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         bf.bf_filter_host(plan, hin, hout, variant, sp)
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e_value = ws * e2e_steps * pixels / e2e_s / 1e6
+    e2e_s = reduce_max(time.perf_counter() - t0, dist)
+    e2e_value = whole_job_mpx(ws, e2e_steps, pixels, e2e_s)
 
     # ---- the plain FP32 path on the same workload, for the fused-vs-FP32 ratio
     fp32_mpx = None

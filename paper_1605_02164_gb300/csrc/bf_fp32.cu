@@ -252,7 +252,10 @@ int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int 
     const size_t bytes = g.smem_floats * sizeof(float);
     if (bytes > (size_t)max_smem) return BF_ERR_UNSUPPORTED;
     cudaError_t e = cudaFuncSetAttribute(mcsf_fp32_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return BF_ERR_CUDA;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
     dim3 grid(cdiv(W, kBX), cdiv(H, BY));
     mcsf_fp32_kernel<D><<<grid, kThreads, bytes, s>>>(in, out, H, W, pitch, p.nu_hi, p.nu_lo, p.K, p.taps, g);
     return cuda_err(cudaGetLastError());

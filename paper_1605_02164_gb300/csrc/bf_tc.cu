@@ -26,13 +26,14 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "bf_internal.cuh"
 
 namespace bf {
 namespace {
 
-constexpr int kT = 256;        // threads per CTA (8 warps)
+constexpr int kT = 256;  // 8 warps: channels, transpose, combine; lane 0 of warps 0 and 4-7 also issue MMAs
 constexpr int kBX = 64;        // output columns per tile
 constexpr int kNC = 8;         // 16-row chunks per region (128 rows)
 constexpr uint32_t kColF = 0;  // TMEM columns: region f (384), D1 (64), D2 (64)
@@ -40,10 +41,19 @@ constexpr uint32_t kColD1 = 384;
 constexpr uint32_t kColD2 = 448;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSpinLimit = 1 << 22;
+// Centre ring: float2 (cos, sin) per output column, rows = flat region rows mod
+// ringC = 16 (lag + 3) (a multiple of 16, so slot & 15 is the row in its chunk);
+// column c of slot row t is stored at t * kBX + (c ^ (t & 15)) so that the 16
+// rows a warp writes at one column and the 32 columns it reads in one row both
+// fall on distinct banks.
+__device__ __forceinline__ int ring_idx(int slot, int col) { return slot * kBX + (col ^ (slot & 15)); }
 
 struct TcGeom {
-    int r, lag, Kw, ksteps, BY, ringC;
-    uint32_t offA2, offB, offC;
+    int r, lag;
+    int Kw, ksteps;    // vertical pass: window rows 16 (lag + 1), K-steps of 16
+    int Kw1, ks1;      // horizontal pass: 64 + 2r rounded up to 16, K-steps of 16
+    int BY, ringC, nc;  // output rows per tile, centre-ring rows, 16-row chunks per term
+    uint32_t offA2, offB1, offB, offC;
     uint32_t smem;
 };
 
@@ -60,9 +70,9 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 // Instruction descriptor, kind::f16: FP32 accumulator, A/B FP16 (0) or
-// BF16 (1), A major-ness (0 K-major, 1 MN-major), B K-major, M = 128, N = 16.
-__device__ __forceinline__ uint32_t idesc(uint32_t ab_fmt, uint32_t a_mn) {
-    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | (a_mn << 15) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+// BF16 (1), A major-ness (0 K-major, 1 MN-major), B K-major, M = 128, N.
+__device__ __forceinline__ uint32_t idesc(uint32_t ab_fmt, uint32_t a_mn, uint32_t n) {
+    return (1u << 4) | (ab_fmt << 7) | (ab_fmt << 10) | (a_mn << 15) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t id, uint32_t acc) {
@@ -137,29 +147,65 @@ __device__ __forceinline__ uint32_t pack2(float a, float b) {
     }
 }
 
+// Element-pair packing and products for the FP16 / BF16 operands.
+template <bool BF16>
+struct Pair;
+template <>
+struct Pair<false> {
+    using T = __half2;
+    static __device__ __forceinline__ T make(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <>
+struct Pair<true> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ T make(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <typename T>
+__device__ __forceinline__ uint32_t bits(T v) {
+    static_assert(sizeof(T) == 4, "packed pair");
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    return u;
+}
+
+// Software pipeline over the flat sequence of (term, 16-row chunk) steps
+// s = k * nc + c (nc = 16-row chunks per term).  Warps 0-7 (compute) in step s
+//   1  build the channels of chunk s+1 (A) into the A1 buffer not being read,
+//   1b wait for the vertical MMAs issued in step s-1 and combine them (C),
+//   2  wait for the horizontal MMAs of chunk s and move D1 into the ring (X),
+//   3  meet warp 8 at one barrier;
+// warp 8 (issue) then issues the horizontal MMAs of chunk s+1 (one chain of
+// N = 64, K = 64 + 2r) and, when chunk s completes 16 output rows, their
+// vertical MMAs (4 M-tiles, N = 16, K = 16 + 16 ceil(2r/16)).  Each MMA group
+// runs while the compute warps do a full step of other work.
+// TMEM: region f 0..383, D1 384..447, D2 448..511 (single-buffered: each is
+// read back before the group that rewrites it is issued).
 template <int NOC, bool BF16>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const float *__restrict__ in, float *__restrict__ out, int H, int W, int pitch,
                    const float *__restrict__ nu_hi, int K, const uint16_t *__restrict__ taps, TcGeom g,
                    int *__restrict__ status) {
+    using P2 = Pair<BF16>;
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t taddr_s;
     __shared__ int abort_s;
 
-    uint8_t *A1 = sm;                 // [mg 16][kg 16][8 rows][16 B]   K-major
-    uint8_t *A2 = sm + g.offA2;       // [kg Kw/8][tile 4][mg 16][8][16 B]  MN-major ring
-    uint8_t *Bt = sm + g.offB;        // [kg Kw/8][ng 2][8 n][16 B]  K-major Toeplitz band
-    float2 *ring = reinterpret_cast<float2 *>(sm + g.offC);  // [ringC][64] centre (cos, sin)
+    uint8_t *A1 = sm;             // 2 x [mg 16][kg 16][8 rows][16 B]   K-major (double buffer)
+    uint8_t *A2 = sm + g.offA2;   // [kg Kw/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
+    uint8_t *B1 = sm + g.offB1;   // [kg Kw1/8][ng 8][8 n][16 B]  K-major band, horizontal pass (N = 64)
+    uint8_t *B2 = sm + g.offB;    // [kg Kw/8][ng 2][8 n][16 B]   K-major band, vertical pass (N = 16)
+    float2 *ring = reinterpret_cast<float2 *>(sm + g.offC);  // [ringC][64] centre (cos, sin), see ring_idx
 
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = w >> 2;
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1;
     const int r = g.r, BY = g.BY;
     const int tx0 = blockIdx.x * kBX, ty0 = blockIdx.y * BY;
     const int rx0 = tx0 - r, ry0 = ty0 - r;
     const size_t plane = (size_t)H * pitch;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+    const int row = l & 15, xg = 2 * w + (l >> 4);
 
-    // ---- set-up: tensor memory, barriers, Toeplitz band ------------------------
+    // ---- set-up: tensor memory, barriers, Toeplitz bands ------------------------
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
                      "r"(kTmemCols)
@@ -168,14 +214,19 @@ __global__ void __launch_bounds__(kT, 1)
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[1])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&mbar[1])) : "memory");  // 4 issuers
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
+    }
+    for (int i = tid; i < g.Kw1 * 64; i += kT) {
+        const int k = i >> 6, n = i & 63, u = k - n;
+        const uint16_t v = (u >= 0 && u <= 2 * r) ? taps[u] : (uint16_t)0;
+        *reinterpret_cast<uint16_t *>(B1 + ((k >> 3) * 8 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
     }
     for (int i = tid; i < g.Kw * 16; i += kT) {
         const int k = i >> 4, n = i & 15, u = k - n;
         const uint16_t v = (u >= 0 && u <= 2 * r) ? taps[u] : (uint16_t)0;
-        *reinterpret_cast<uint16_t *>(Bt + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
+        *reinterpret_cast<uint16_t *>(B2 + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
     }
     fence_async_smem();
     fence_before();
@@ -183,29 +234,38 @@ __global__ void __launch_bounds__(kT, 1)
     fence_after();
     const uint32_t tmem = taddr_s;
 
-    // ---- region f -> tensor memory (FP32, resident for all terms) -------------
-    // thread (w, l) owns region row 16c + (l & 15), columns 8 xg .. 8 xg + 7
-    // with xg = 2w + (l >> 4), stored in its own TMEM lane at columns
-    // (2c + h) * 24 + ch * 8 + j.
-    const int row = l & 15, xg = 2 * w + (l >> 4);
-    for (int c = 0; c < kNC; ++c) {
-        const int gy = ry0 + 16 * c + row;
-        const bool rowv = gy >= 0 && gy < H;
+    // ---- region f -> tensor memory; in-image masks (compute warps) ------------
+    // Thread (w, l) owns region row 16c + row, columns 8 xg .. 8 xg + 7 of
+    // every chunk c, stored in its TMEM lane at columns (2c + h)*24 + ch*8 + j.
+    uint64_t vmask = 0;  // bit 8c + j: pixel inside the image
+    uint32_t cmask = 0;  // bit j: column is a centre (output) column
+    {
 #pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            float v[8];
+        for (int j = 0; j < 8; ++j) {
+            const int cx = 8 * xg + j - r;
+            if (cx >= 0 && cx < kBX) cmask |= 1u << j;
+        }
+        for (int c = 0; c < kNC; ++c) {
+            const int gy = ry0 + 16 * c + row;
+            const bool rowv = gy >= 0 && gy < H;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int gx = rx0 + 8 * xg + j;
-                v[j] = (rowv && gx >= 0 && gx < W) ? __ldg(in + ch * plane + (size_t)gy * pitch + gx) : 0.f;
+                if (rowv && gx >= 0 && gx < W) vmask |= 1ull << (8 * c + j);
             }
-            tmem_st8(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8, v);
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    v[j] = ((vmask >> (8 * c + j)) & 1)
+                               ? __ldg(in + ch * plane + (size_t)(ry0 + 16 * c + row) * pitch + (rx0 + 8 * xg + j))
+                               : 0.f;
+                tmem_st8(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8, v);
+            }
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     }
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    fence_before();
-    __syncthreads();
-    fence_after();
 
     float acc[NOC][16];
 #pragma unroll
@@ -213,161 +273,203 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[o][j] = 0.f;
 
-    const uint32_t idA1 = idesc(BF16 ? 1u : 0u, 0u);
-    const uint32_t idA2 = idesc(BF16 ? 1u : 0u, 1u);
-    const uint32_t a1s = smem_u32(A1), a2s = smem_u32(A2), bts = smem_u32(Bt);
-    const int kgring = g.Kw >> 3;
-    uint32_t ph0 = 0, ph1 = 0;
+    const int NCr = g.nc;  // 16-row chunks per term: ceil((BY + 2r) / 16) <= 8
+    const int S = K * NCr;
+    uint32_t ph1 = 0, ph2 = 0;
+    int pend_oc = -1, pend_sfirst = 0;
     bool timed_out = false;
 
-    for (int k = 0; k < K; ++k) {
+    // A: channels of flat step s into A1[s & 1] (compute warps)
+    auto stage_A = [&](int s) {
+        const int k = s / NCr, c = s - k * NCr;
         const float n0 = __ldg(nu_hi + 3 * k), n1 = __ldg(nu_hi + 3 * k + 1), n2 = __ldg(nu_hi + 3 * k + 2);
-        for (int c = 0; c < kNC; ++c) {
-            // ---------------- A: cos/sin and modulated channels ----------------
-            {
-                float f0[8], f1[8], f2[8];
-                const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24;
-                tmem_ld8(fa, f0);
-                tmem_ld8(fa + 8, f1);
-                tmem_ld8(fa + 16, f2);
-                tmem_wait_ld();
-                const int ry = 16 * c + row, gy = ry0 + ry;
-                const bool rowv = gy >= 0 && gy < H;
-                float cs[8], sn[8];
+        float f0[8], f1[8], f2[8];
+        const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24;
+        tmem_ld8(fa, f0);
+        tmem_ld8(fa + 8, f1);
+        tmem_ld8(fa + 16, f2);
+        tmem_wait_ld();
+        const uint32_t vm = (uint32_t)(vmask >> (8 * c)) & 0xFFu;
+        const int ry = 16 * c + row;
+        const bool centre_row = ry >= r && ry < r + BY && cmask;
+        uint32_t o[8][4];
+        float csv[8], snv[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int gx = rx0 + 8 * xg + j;
-                    const bool v = rowv && gx >= 0 && gx < W;
-                    const float t = fmaf(n0, f0[j], fmaf(n1, f1[j], n2 * f2[j]));
-                    const float fr = t - rintf(t);
-                    float s_, c_;
-                    __sincosf(6.28318530717958647692f * fr, &s_, &c_);
-                    cs[j] = v ? c_ : 0.f;
-                    sn[j] = v ? s_ : 0.f;
-                }
-                uint8_t *dst = A1 + (size_t)(xg * 128 + (row & 7) * 16);
-                const int mg0 = row >> 3;  // + 2 * ch
-                uint4 pk;
-#define BF_STORE_CH(CH, EXPR)                                                                             \
-    {                                                                                                     \
-        uint32_t u[4];                                                                                    \
-        _Pragma("unroll") for (int p = 0; p < 4; ++p) {                                                   \
-            const int j = 2 * p;                                                                          \
-            float e0, e1;                                                                                 \
-            {                                                                                             \
-                const int jj = j;                                                                         \
-                e0 = (EXPR);                                                                              \
-            }                                                                                             \
-            {                                                                                             \
-                const int jj = j + 1;                                                                     \
-                e1 = (EXPR);                                                                              \
-            }                                                                                             \
-            u[p] = pack2<BF16>(e0, e1);                                                                   \
-        }                                                                                                 \
-        pk = make_uint4(u[0], u[1], u[2], u[3]);                                                          \
-        *reinterpret_cast<uint4 *>(dst + (size_t)((2 * (CH) + mg0) * 16) * 128) = pk;                     \
-    }
-                BF_STORE_CH(0, cs[jj] * f0[jj]);
-                BF_STORE_CH(1, cs[jj] * f1[jj]);
-                BF_STORE_CH(2, cs[jj] * f2[jj]);
-                BF_STORE_CH(3, cs[jj]);
-                BF_STORE_CH(4, sn[jj] * f0[jj]);
-                BF_STORE_CH(5, sn[jj] * f1[jj]);
-                BF_STORE_CH(6, sn[jj] * f2[jj]);
-                BF_STORE_CH(7, sn[jj]);
-#undef BF_STORE_CH
-                // centre cos/sin of output pixels, kept for the combine
-                if (ry >= r && ry < r + BY) {
-                    float2 *rrow = ring + (size_t)(ry % g.ringC) * kBX;
+        for (int p = 0; p < 4; ++p) {
+            float cv[2], sv[2];
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int cx = 8 * xg + j - r;
-                        if (cx >= 0 && cx < kBX) rrow[cx] = make_float2(cs[j], sn[j]);
-                    }
-                }
+            for (int e = 0; e < 2; ++e) {
+                const int j = 2 * p + e;
+                const float t = fmaf(n0, f0[j], fmaf(n1, f1[j], n2 * f2[j]));
+                const float fr = t - rintf(t);
+                float s_, c_;
+                __sincosf(6.28318530717958647692f * fr, &s_, &c_);
+                const bool v = (vm >> j) & 1u;
+                cv[e] = v ? c_ : 0.f;
+                sv[e] = v ? s_ : 0.f;
+                csv[j] = cv[e];
+                snv[j] = sv[e];
             }
-            fence_async_smem();
-            __syncthreads();
-            if (abort_s) goto cleanup;
-            // ---------------- M1: horizontal pass ------------------------------
-            if (tid == 0) {
-                fence_after();
-#pragma unroll 1
-                for (int nc = 0; nc < 4; ++nc)
-#pragma unroll 1
-                    for (int ks = 0; ks < g.ksteps; ++ks)
-                        mma_f16(tmem + kColD1 + 16 * nc, sdesc(a1s + 2 * (nc + ks) * 128, 128, 2048),
-                                sdesc(bts + ks * 512, 256, 128), idA1, ks > 0);
-                mma_commit(&mbar[0]);
+            const typename P2::T hc = P2::make(cv[0], cv[1]);
+            const typename P2::T hs = P2::make(sv[0], sv[1]);
+            o[3][p] = bits(hc);
+            o[7][p] = bits(hs);
+            if constexpr (BF16) {
+                // BF16 keeps 8 mantissa bits: form the products in FP32 and round once
+                o[0][p] = bits(P2::make(cv[0] * f0[2 * p], cv[1] * f0[2 * p + 1]));
+                o[1][p] = bits(P2::make(cv[0] * f1[2 * p], cv[1] * f1[2 * p + 1]));
+                o[2][p] = bits(P2::make(cv[0] * f2[2 * p], cv[1] * f2[2 * p + 1]));
+                o[4][p] = bits(P2::make(sv[0] * f0[2 * p], sv[1] * f0[2 * p + 1]));
+                o[5][p] = bits(P2::make(sv[0] * f1[2 * p], sv[1] * f1[2 * p + 1]));
+                o[6][p] = bits(P2::make(sv[0] * f2[2 * p], sv[1] * f2[2 * p + 1]));
+            } else {
+                // FP16 (11-bit mantissa): packed half2 products of rounded operands
+                const typename P2::T g0 = P2::make(f0[2 * p], f0[2 * p + 1]);
+                const typename P2::T g1 = P2::make(f1[2 * p], f1[2 * p + 1]);
+                const typename P2::T g2 = P2::make(f2[2 * p], f2[2 * p + 1]);
+                o[0][p] = bits(__hmul2(hc, g0));
+                o[1][p] = bits(__hmul2(hc, g1));
+                o[2][p] = bits(__hmul2(hc, g2));
+                o[4][p] = bits(__hmul2(hs, g0));
+                o[5][p] = bits(__hmul2(hs, g1));
+                o[6][p] = bits(__hmul2(hs, g2));
             }
-            if (!mbar_wait(&mbar[0], ph0)) timed_out = true;
-            ph0 ^= 1;
-            fence_after();
-            // ---------------- X: D1 -> ring of blurred rows --------------------
-            {
-                float v[32];
-                const uint32_t da = tmem + lane_base + kColD1 + 32 * h;
-                tmem_ld16(da, v);
-                tmem_ld16(da + 16, v + 16);
-                tmem_wait_ld();
-                const int ch = 2 * q + (l >> 4), gsel = ch >> 2, p = ch & 3;
-                const int kr = (16 * c + row) % g.Kw;
-                uint8_t *base = A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16;
+        }
+        if (centre_row) {  // centre cos/sin for the combine, slot = flat region row mod 128
+            const int slot = (16 * s + row) % g.ringC;
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    uint4 pk = make_uint4(pack2<BF16>(v[8 * i], v[8 * i + 1]), pack2<BF16>(v[8 * i + 2], v[8 * i + 3]),
-                                          pack2<BF16>(v[8 * i + 4], v[8 * i + 5]),
-                                          pack2<BF16>(v[8 * i + 6], v[8 * i + 7]));
-                    *reinterpret_cast<uint4 *>(base + (p * 4 + i) * 128) = pk;
-                }
-            }
-            fence_before();
-            fence_async_smem();
-            if (timed_out) abort_s = 1;
-            __syncthreads();
-            if (abort_s) goto cleanup;
-            // ---------------- M2 + C: vertical pass and combine ----------------
-            {
-                const int oc = c - g.lag;
-                if (oc >= 0 && oc < NOC && 16 * oc < BY) {
-                    if (tid == 0) {
-                        fence_after();
-#pragma unroll 1
-                        for (int t = 0; t < 4; ++t)
-#pragma unroll 1
-                            for (int ks = 0; ks < g.ksteps; ++ks) {
-                                const int kg0 = (2 * oc + 2 * ks) % kgring;
-                                mma_f16(tmem + kColD2 + 16 * t, sdesc(a2s + kg0 * 8192 + t * 2048, 8192, 128),
-                                        sdesc(bts + ks * 512, 256, 128), idA2, ks > 0);
-                            }
-                        mma_commit(&mbar[1]);
-                    }
-                    if (!mbar_wait(&mbar[1], ph1)) timed_out = true;
-                    ph1 ^= 1;
-                    fence_after();
-                    float vc[16], vs[16];
-                    tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h), vc);
-                    tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h + 1), vs);
-                    tmem_wait_ld();
-                    const int x = 32 * h + l;
+            for (int j = 0; j < 8; ++j)
+                if ((cmask >> j) & 1u) ring[ring_idx(slot, 8 * xg + j - r)] = make_float2(csv[j], snv[j]);
+        }
+        uint8_t *dst = A1 + (s & 1) * 32768 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048;
 #pragma unroll
-                    for (int o = 0; o < NOC; ++o) {
-                        if (o == oc) {
+        for (int ch = 0; ch < 8; ++ch)
+            *reinterpret_cast<uint4 *>(dst + ch * 4096) = make_uint4(o[ch][0], o[ch][1], o[ch][2], o[ch][3]);
+    };
+
+    // C: combine output chunk oc (its window starts at flat step s_first)
+    auto stage_C = [&](int oc, int s_first) {
+        float vc[16], vs[16];
+        tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h), vc);
+        tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h + 1), vs);
+        tmem_wait_ld();
+        const int x = 32 * h + l;
+        int slot = (16 * s_first + r) % g.ringC;  // flat region row of output row 16 oc
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const float2 cs = ring[(size_t)((16 * o + j + r) % g.ringC) * kBX + x];
-                                acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
-                            }
-                        }
-                    }
-                    fence_before();
-                    if (timed_out) abort_s = 1;
+        for (int o = 0; o < NOC; ++o) {
+            if (o == oc) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float2 cs = ring[ring_idx(slot, x)];
+                    if (++slot == g.ringC) slot = 0;
+                    acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
                 }
             }
         }
-        __syncthreads();  // term boundary: centre ring rows are reused from row 0
-        if (abort_s) goto cleanup;
+    };
+
+    // X: D1 of flat step s -> A2 ring
+    auto stage_X = [&](int s) {
+        float v[32];
+        const uint32_t da = tmem + lane_base + kColD1 + 32 * h;
+        tmem_ld16(da, v);
+        tmem_ld16(da + 16, v + 16);
+        tmem_wait_ld();
+        const int ch = 2 * q + (l >> 4), gsel = ch >> 2, p = ch & 3;
+        const int kr = (16 * s + row) % g.Kw;
+        uint8_t *base = A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint4 pk = make_uint4(bits(P2::make(v[8 * i], v[8 * i + 1])), bits(P2::make(v[8 * i + 2], v[8 * i + 3])),
+                                        bits(P2::make(v[8 * i + 4], v[8 * i + 5])),
+                                        bits(P2::make(v[8 * i + 6], v[8 * i + 7])));
+            *reinterpret_cast<uint4 *>(base + i * 128) = pk;
+        }
+    };
+
+    // MMA issue (warp 8, lane 0).  Descriptors are built once; operand offsets
+    // are added to the 14-bit start-address field (address >> 4).
+    const uint64_t dA1 = sdesc(smem_u32(A1), 128, 2048);   // K-major: LBO = next K group, SBO = next 8 rows
+    const uint64_t dB1 = sdesc(smem_u32(B1), 1024, 128);
+    const uint64_t dA2 = sdesc(smem_u32(A2), 8192, 128);   // MN-major: LBO = next K group, SBO = next 8 columns
+    const uint64_t dB2 = sdesc(smem_u32(B2), 256, 128);
+    const uint32_t id1 = idesc(BF16 ? 1u : 0u, 0u, 64u);
+    const uint32_t id2 = idesc(BF16 ? 1u : 0u, 1u, 16u);
+    const int kgring = g.Kw >> 3;
+    auto issue_M1 = [&](int s) {
+        const uint64_t a = dA1 + (uint64_t)((s & 1) * (32768 >> 4));
+#pragma unroll
+        for (int ks = 0; ks < 8; ++ks)
+            if (ks < g.ks1) mma_f16(tmem + kColD1, a + 16 * ks, dB1 + 128 * ks, id1, ks > 0);
+        mma_commit(&mbar[0]);
+    };
+    auto issue_M2 = [&](int s_first, int t) {  // M-tile t of the vertical pass
+        const int kgb = (2 * s_first) % kgring;
+#pragma unroll
+        for (int ks = 0; ks < 5; ++ks)
+            if (ks < g.ksteps) {
+                int kg0 = kgb + 2 * ks;
+                if (kg0 >= kgring) kg0 -= kgring;
+                mma_f16(tmem + kColD2 + 16 * t, dA2 + (uint64_t)((kg0 * 8192 + t * 2048) >> 4), dB2 + 32 * ks, id2,
+                        ks > 0);
+            }
+        mma_commit(&mbar[1]);
+    };
+
+    // ---- prologue ------------------------------------------------------------------
+    stage_A(0);
+    fence_async_smem();
+    __syncthreads();
+    if (w == 0 && l == 0) {
+        fence_after();
+        issue_M1(0);
     }
+
+    // ---- pipeline ----------------------------------------------------------------------
+    for (int s = 0, c = 0; s < S; ++s, c = (c + 1 == NCr) ? 0 : c + 1) {
+        const int oc = c - g.lag;
+        const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
+        if (s + 1 < S) stage_A(s + 1);
+        if (pend_oc >= 0) {
+            if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+            ph2 ^= 1;
+            fence_after();
+            stage_C(pend_oc, pend_sfirst);
+            pend_oc = -1;
+        }
+        if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
+        ph1 ^= 1;
+        fence_after();
+        stage_X(s);
+        fence_before();
+        fence_async_smem();
+        if (timed_out) abort_s = 1;
+        __syncthreads();
+        if (abort_s) goto cleanup;
+        if (l == 0 && (w == 0 || (w >= 4 && do_m2))) {
+            fence_after();
+            if (w == 0) {
+                if (s + 1 < S) issue_M1(s + 1);
+            } else {
+                issue_M2(s - g.lag, w - 4);
+            }
+        }
+        __syncwarp();
+        if (do_m2) {
+            pend_oc = oc;
+            pend_sfirst = s - g.lag;
+        }
+    }
+    if (pend_oc >= 0) {
+        if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+        ph2 ^= 1;
+        fence_after();
+        stage_C(pend_oc, pend_sfirst);
+    }
+    if (timed_out) abort_s = 1;
+    fence_before();
+    __syncthreads();
+    if (abort_s) goto cleanup;
 
     // ---- P / Z ----------------------------------------------------------------
     {
@@ -394,11 +496,11 @@ __global__ void __launch_bounds__(kT, 1)
     }
 
 cleanup:
-    if (abort_s && tid == 0) {
-        atomicCAS(status, 0, BF_ERR_TIMEOUT);
-        // drain: wait (bounded) for every MMA issued by this thread
+    if (abort_s && l == 0 && (w == 0 || w >= 4)) {
+        if (w == 0) atomicCAS(status, 0, BF_ERR_TIMEOUT);
+        // drain: bounded wait for every MMA this thread issued (fresh barrier phase)
         mma_commit(&mbar[0]);
-        mbar_wait(&mbar[0], ph0);
+        mbar_wait(&mbar[0], ph1);
     }
     fence_before();
     __syncthreads();
@@ -410,10 +512,14 @@ template <int NOC, bool BF16>
 int launch_noc(const float *in, float *out, int H, int W, int pitch, const bf_plan_s &p, const TcGeom &g,
                cudaStream_t s) {
     auto kern = mcsf_tc_kernel<NOC, BF16>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem) != cudaSuccess)
-        return BF_ERR_CUDA;
-    int dev = 0;
+    int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if ((int)g.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
     int *st = status_word(dev);
     if (!st) return BF_ERR_NOMEM;
     dim3 grid(cdiv(W, kBX), cdiv(H, g.BY));
@@ -431,15 +537,19 @@ int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int
     g.lag = cdiv(2 * p.r, 16);
     g.Kw = 16 * (g.lag + 1);
     g.ksteps = g.Kw / 16;
-    if (48 + g.Kw > 128) return BF_ERR_UNSUPPORTED;
+    g.Kw1 = 16 * cdiv(kBX + 2 * p.r, 16);
+    g.ks1 = g.Kw1 / 16;
+    if (g.Kw1 > 128 || g.ksteps > 5) return BF_ERR_UNSUPPORTED;
     int noc = (128 - 2 * p.r) / 16;
     if (noc > kNC - g.lag) noc = kNC - g.lag;
-    if (noc > 6) noc = 6;
+    if (noc > 5) noc = 5;
     if (noc < 4) return BF_ERR_UNSUPPORTED;
     g.BY = 16 * noc;
-    g.ringC = 16 * (g.lag + 2);
-    g.offA2 = 32768;
-    g.offB = g.offA2 + (uint32_t)(g.Kw / 8) * 8192;
+    g.nc = cdiv(g.BY + 2 * p.r, 16);
+    g.ringC = 16 * (g.lag + 3);  // rows written ahead by stage A never reach the rows stage C reads
+    g.offA2 = 65536;
+    g.offB1 = g.offA2 + (uint32_t)(g.Kw / 8) * 8192;
+    g.offB = g.offB1 + (uint32_t)g.Kw1 * 128;
     g.offC = g.offB + (uint32_t)g.Kw * 32;
     g.offC = (g.offC + 127) & ~127u;
     const uint32_t ring_bytes = (uint32_t)g.ringC * kBX * 8;
@@ -450,7 +560,6 @@ int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int
     switch (noc) {
         case 4: return bf ? launch_noc<4, true>(in, out, H, W, pitch, p, g, s) : launch_noc<4, false>(in, out, H, W, pitch, p, g, s);
         case 5: return bf ? launch_noc<5, true>(in, out, H, W, pitch, p, g, s) : launch_noc<5, false>(in, out, H, W, pitch, p, g, s);
-        case 6: return bf ? launch_noc<6, true>(in, out, H, W, pitch, p, g, s) : launch_noc<6, false>(in, out, H, W, pitch, p, g, s);
         default: return BF_ERR_UNSUPPORTED;
     }
 }

@@ -59,6 +59,7 @@ def _check_fp32(got, res, s, r, tol=FP32_TOL, lowz_frac=0.0):
     mask = res["Zre"] >= _zmin(s, r)
     assert (~mask).mean() <= lowz_frac
     err = np.abs(got - res["S"])[:, mask]
+    print(f"fp32 parity: max-abs {err.max():.4e}  low-Z {(~mask).sum()}")
     assert np.isfinite(got).all()
     assert err.max() <= tol, f"max-abs {err.max():.3e}"
     return float(err.max())
@@ -252,6 +253,7 @@ def _check_tc(got, S, Z, s, r, lowz_frac=0.0):
     assert np.isfinite(got).all()
     err = np.abs(got - S)[:, mask]
     psnr = O.psnr(S, got)
+    print(f"tc parity: max-abs {err.max():.4e}  PSNR {psnr:.2f} dB  low-Z {(~mask).sum()}")
     assert err.max() <= TC_MAXABS, f"max-abs {err.max():.3e}"
     assert psnr >= TC_PSNR, f"PSNR {psnr:.2f} dB"
     return float(err.max()), psnr
