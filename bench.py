@@ -319,7 +319,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="fp32", choices=["fp32", "fp16tc", "bf16tc"])
+    ap.add_argument("--variant", default="fp16tc", choices=["fp32", "fp16tc", "bf16tc"])
     ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--seed", type=int, default=3000)
     ap.add_argument("--cpu-crop", type=int, default=1536)
