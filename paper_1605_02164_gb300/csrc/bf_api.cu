@@ -3,6 +3,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <mutex>
 #include <vector>
 
@@ -29,6 +30,42 @@ int check_image_args(const bf_plan_s *p, const float *in, const float *out, int 
     return BF_OK;
 }
 }  // namespace
+
+void *stream_scratch(cudaStream_t stream, size_t bytes) {
+    struct Slot {
+        int device;
+        cudaStream_t stream;
+        void *ptr;
+        size_t bytes;
+    };
+    static std::mutex mu;
+    static std::vector<Slot> slots;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    for (Slot &sl : slots)
+        if (sl.device == dev && sl.stream == stream) {
+            if (sl.bytes >= bytes) return sl.ptr;
+            cudaStreamSynchronize(stream);  // the old buffer may still be read by queued work
+            cudaFree(sl.ptr);
+            sl.ptr = nullptr;
+            sl.bytes = 0;
+            size_t grow = std::max(bytes, (size_t)64 << 10);
+            if (cudaMalloc(&sl.ptr, grow) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            sl.bytes = grow;
+            return sl.ptr;
+        }
+    Slot sl{dev, stream, nullptr, std::max(bytes, (size_t)64 << 10)};
+    if (cudaMalloc(&sl.ptr, sl.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    slots.push_back(sl);
+    return sl.ptr;
+}
 
 int *status_word(int device) {
     if (device < 0 || device >= 64) return nullptr;
@@ -67,10 +104,21 @@ extern "C" int bf_filter_batch(const bf_item *items, int n, int variant, void *s
                                       items[i].pitch);
         if (rc != BF_OK) return rc;
     }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (variant == BF_FP16TC || variant == BF_BF16TC) {
+        // every image's tiles in one persistent launch
+        void *scratch = bf::stream_scratch(s, bf::tc_scratch_bytes(n));
+        int dev = 0;
+        cudaGetDevice(&dev);
+        int *st = bf::status_word(dev);
+        if (!scratch || !st) return BF_ERR_NOMEM;
+        return bf::tc_launch_batch(items, n, variant, scratch, st, s);
+    }
+    if (variant != BF_FP32) return BF_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         const bf_item &it = items[i];
         if (it.H == 0 || it.W == 0) continue;
-        int rc = bf_filter(it.plan, it.in, it.out, it.H, it.W, it.pitch, variant, stream);
+        int rc = bf::launch_fp32(*it.plan, it.in, it.out, it.H, it.W, it.pitch, s);
         if (rc != BF_OK) return rc;
     }
     return BF_OK;

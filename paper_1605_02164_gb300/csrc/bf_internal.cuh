@@ -42,6 +42,14 @@ int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, i
 // Tensor-core fused kernel (csrc/bf_tc.cu); variant BF_FP16TC or BF_BF16TC.
 int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int variant,
               cudaStream_t s);
+// One persistent launch over all tiles of n images (d = 3).  `scratch` holds
+// tc_scratch_bytes(n) bytes of device memory used only by this launch's stream.
+size_t tc_scratch_bytes(int n);
+int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s);
+
+// Library-owned device scratch for work issued on `stream`, at least `bytes`
+// long (grown on demand; calls on one stream are ordered, so they may share it).
+void *stream_scratch(cudaStream_t stream, size_t bytes);
 
 inline int cuda_err(cudaError_t e) { return e == cudaSuccess ? BF_OK : BF_ERR_CUDA; }
 

@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "bf_internal.cuh"
 
 namespace bf {
@@ -36,6 +39,7 @@ namespace {
 constexpr int kT = 256;  // 8 warps: channels, transpose, combine; lane 0 of warps 0 and 4-7 also issue MMAs
 constexpr int kBX = 64;        // output columns per tile
 constexpr int kNC = 8;         // 16-row chunks per region (128 rows)
+constexpr int kNOC = 5;        // output chunks (of 16 rows) per tile at most
 constexpr uint32_t kColF = 0;  // TMEM columns: region f (384), D1 (64), D2 (64)
 constexpr uint32_t kColD1 = 384;
 constexpr uint32_t kColD2 = 448;
@@ -48,14 +52,30 @@ constexpr int kSpinLimit = 1 << 22;
 // fall on distinct banks.
 __device__ __forceinline__ int ring_idx(int slot, int col) { return slot * kBX + (col ^ (slot & 15)); }
 
-struct TcGeom {
+// One image of a launch (the single-image call is a batch of one).  The table
+// lives in device memory; tiles of all images form one work queue.
+struct TcImg {
+    const float *in;
+    float *out;
+    const float *nu_hi;     // K x 3 frequencies (turns), FP32
+    const uint16_t *taps;   // FP16 or BF16 bits of the normalised 1-D taps
+    int H, W, pitch, K;
     int r, lag;
-    int Kw, ksteps;    // vertical pass: window rows 16 (lag + 1), K-steps of 16
-    int Kw1, ks1;      // horizontal pass: 64 + 2r rounded up to 16, K-steps of 16
-    int BY, ringC, nc;  // output rows per tile, centre-ring rows, 16-row chunks per term
-    uint32_t offA2, offB1, offB, offC;
-    uint32_t smem;
+    int Kw, ksteps;         // vertical pass: window rows 16 (lag + 1), K-steps of 16
+    int Kw1, ks1;           // horizontal pass: 64 + 2r rounded up to 16, K-steps of 16
+    int BY, nc, ringC;      // output rows per tile, 16-row chunks per term, centre-ring rows
+    int tiles_x, tile_begin, pad;
 };
+static_assert(sizeof(TcImg) == 96, "descriptor layout");
+
+// Shared-memory layout of a launch, sized for the largest window in it.
+struct TcLayout {
+    uint32_t offA2, offB1, offB, offC, smem;
+};
+
+// Launch control words kept in device scratch: [0] tile counter (zeroed by
+// the copy that uploads the image table before every launch).
+constexpr int kCtrlWords = 64;  // 256 bytes, so the descriptor table after it stays 256-byte aligned
 
 __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
@@ -168,44 +188,43 @@ __device__ __forceinline__ uint32_t bits(T v) {
     return u;
 }
 
-// Software pipeline over the flat sequence of (term, 16-row chunk) steps
-// s = k * nc + c (nc = 16-row chunks per term).  Warps 0-7 (compute) in step s
+// Persistent kernel: each CTA keeps its tensor memory and pops tiles (of all
+// images) from a device work counter until the queue is empty.
+// Per tile, a software pipeline over the flat sequence of (term, 16-row chunk)
+// steps s = k * nc + c.  All 8 warps in step s
 //   1  build the channels of chunk s+1 (A) into the A1 buffer not being read,
 //   1b wait for the vertical MMAs issued in step s-1 and combine them (C),
 //   2  wait for the horizontal MMAs of chunk s and move D1 into the ring (X),
-//   3  meet warp 8 at one barrier;
-// warp 8 (issue) then issues the horizontal MMAs of chunk s+1 (one chain of
-// N = 64, K = 64 + 2r) and, when chunk s completes 16 output rows, their
-// vertical MMAs (4 M-tiles, N = 16, K = 16 + 16 ceil(2r/16)).  Each MMA group
-// runs while the compute warps do a full step of other work.
+//   3  meet at one barrier;
+// then lane 0 of warp 0 issues the horizontal MMAs of chunk s+1 (one chain of
+// N = 64, K = 64 + 2r) and, when chunk s completes 16 output rows, lane 0 of
+// warps 4-7 each issue one vertical M-tile (N = 16, K = 16 + 16 ceil(2r/16)).
+// Each MMA group runs while the warps do a full step of other work.
 // TMEM: region f 0..383, D1 384..447, D2 448..511 (single-buffered: each is
 // read back before the group that rewrites it is issued).
-template <int NOC, bool BF16>
+template <bool BF16>
 __global__ void __launch_bounds__(kT, 1)
-    mcsf_tc_kernel(const float *__restrict__ in, float *__restrict__ out, int H, int W, int pitch,
-                   const float *__restrict__ nu_hi, int K, const uint16_t *__restrict__ taps, TcGeom g,
-                   int *__restrict__ status) {
+    mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
+                   int *__restrict__ status, TcLayout lay) {
+    constexpr int NOC = kNOC;
     using P2 = Pair<BF16>;
     extern __shared__ __align__(1024) uint8_t sm[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t taddr_s;
-    __shared__ int abort_s;
+    __shared__ int abort_s, tile_s;
 
-    uint8_t *A1 = sm;             // 2 x [mg 16][kg 16][8 rows][16 B]   K-major (double buffer)
-    uint8_t *A2 = sm + g.offA2;   // [kg Kw/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
-    uint8_t *B1 = sm + g.offB1;   // [kg Kw1/8][ng 8][8 n][16 B]  K-major band, horizontal pass (N = 64)
-    uint8_t *B2 = sm + g.offB;    // [kg Kw/8][ng 2][8 n][16 B]   K-major band, vertical pass (N = 16)
-    float2 *ring = reinterpret_cast<float2 *>(sm + g.offC);  // [ringC][64] centre (cos, sin), see ring_idx
+    uint8_t *A1 = sm;               // 2 x [mg 16][kg 16][8 rows][16 B]   K-major (double buffer)
+    uint8_t *A2 = sm + lay.offA2;   // [kg Kw/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
+    uint8_t *B1 = sm + lay.offB1;   // [kg Kw1/8][ng 8][8 n][16 B]  K-major band, horizontal pass (N = 64)
+    uint8_t *B2 = sm + lay.offB;    // [kg Kw/8][ng 2][8 n][16 B]   K-major band, vertical pass (N = 16)
+    float2 *ring = reinterpret_cast<float2 *>(sm + lay.offC);  // [ringC][64] centre (cos, sin), see ring_idx
+    int *counter = ctrl;
 
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1;
-    const int r = g.r, BY = g.BY;
-    const int tx0 = blockIdx.x * kBX, ty0 = blockIdx.y * BY;
-    const int rx0 = tx0 - r, ry0 = ty0 - r;
-    const size_t plane = (size_t)H * pitch;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     const int row = l & 15, xg = 2 * w + (l >> 4);
 
-    // ---- set-up: tensor memory, barriers, Toeplitz bands ------------------------
+    // ---- once per CTA: tensor memory, barriers ------------------------------------
     if (w == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
                      "r"(kTmemCols)
@@ -218,28 +237,58 @@ __global__ void __launch_bounds__(kT, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_s = 0;
     }
-    for (int i = tid; i < g.Kw1 * 64; i += kT) {
-        const int k = i >> 6, n = i & 63, u = k - n;
-        const uint16_t v = (u >= 0 && u <= 2 * r) ? taps[u] : (uint16_t)0;
-        *reinterpret_cast<uint16_t *>(B1 + ((k >> 3) * 8 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
-    }
-    for (int i = tid; i < g.Kw * 16; i += kT) {
-        const int k = i >> 4, n = i & 15, u = k - n;
-        const uint16_t v = (u >= 0 && u <= 2 * r) ? taps[u] : (uint16_t)0;
-        *reinterpret_cast<uint16_t *>(B2 + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
-    }
-    fence_async_smem();
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = taddr_s;
+    const uint64_t dA1 = sdesc(smem_u32(A1), 128, 2048);   // K-major: LBO = next K group, SBO = next 8 rows
+    const uint64_t dB1 = sdesc(smem_u32(B1), 1024, 128);
+    const uint64_t dA2 = sdesc(smem_u32(A2), 8192, 128);   // MN-major: LBO = next K group, SBO = next 8 columns
+    const uint64_t dB2 = sdesc(smem_u32(B2), 256, 128);
+    const uint32_t id1 = idesc(BF16 ? 1u : 0u, 0u, 64u);
+    const uint32_t id2 = idesc(BF16 ? 1u : 0u, 1u, 16u);
+    uint32_t ph1 = 0, ph2 = 0;  // barrier phases carry over from tile to tile
+    int band_r = -1;            // window radius the Toeplitz bands in smem were built for
+    bool timed_out = false;
 
-    // ---- region f -> tensor memory; in-image masks (compute warps) ------------
-    // Thread (w, l) owns region row 16c + row, columns 8 xg .. 8 xg + 7 of
-    // every chunk c, stored in its TMEM lane at columns (2c + h)*24 + ch*8 + j.
-    uint64_t vmask = 0;  // bit 8c + j: pixel inside the image
-    uint32_t cmask = 0;  // bit j: column is a centre (output) column
-    {
+    for (;;) {
+        // ---- next tile -------------------------------------------------------------
+        if (tid == 0) tile_s = atomicAdd(counter, 1);
+        __syncthreads();
+        const int tile = tile_s;
+        if (tile >= total_tiles) break;
+        int im = 0;
+        while (im + 1 < n_imgs && __ldg(&imgs[im + 1].tile_begin) <= tile) ++im;
+        const TcImg g = imgs[im];
+        const float *__restrict__ in = g.in;
+        float *__restrict__ out = g.out;
+        const float *__restrict__ nu_hi = g.nu_hi;
+        const int H = g.H, W = g.W, pitch = g.pitch, K = g.K, r = g.r, BY = g.BY;
+        const int tl = tile - g.tile_begin;
+        const int ty = tl / g.tiles_x, tx = tl - ty * g.tiles_x;
+        const int tx0 = tx * kBX, ty0 = ty * BY;
+        const int rx0 = tx0 - r, ry0 = ty0 - r;
+        const size_t plane = (size_t)H * pitch;
+
+        if (r != band_r) {  // Toeplitz bands of the normalised taps (uniform across the CTA)
+            for (int i = tid; i < g.Kw1 * 64; i += kT) {
+                const int k = i >> 6, n = i & 63, u = k - n;
+                const uint16_t v = (u >= 0 && u <= 2 * r) ? g.taps[u] : (uint16_t)0;
+                *reinterpret_cast<uint16_t *>(B1 + ((k >> 3) * 8 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
+            }
+            for (int i = tid; i < g.Kw * 16; i += kT) {
+                const int k = i >> 4, n = i & 15, u = k - n;
+                const uint16_t v = (u >= 0 && u <= 2 * r) ? g.taps[u] : (uint16_t)0;
+                *reinterpret_cast<uint16_t *>(B2 + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
+            }
+            band_r = r;
+        }
+
+        // ---- region f -> tensor memory; in-image masks -------------------------------
+        // Thread (w, l) owns region row 16c + row, columns 8 xg .. 8 xg + 7 of
+        // every chunk c, stored in its TMEM lane at columns (2c + h)*24 + ch*8 + j.
+        uint64_t vmask = 0;  // bit 8c + j: pixel inside the image
+        uint32_t cmask = 0;  // bit j: column is a centre (output) column
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const int cx = 8 * xg + j - r;
@@ -265,234 +314,232 @@ __global__ void __launch_bounds__(kT, 1)
             }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-    }
 
-    float acc[NOC][16];
+        float acc[NOC][16];
 #pragma unroll
-    for (int o = 0; o < NOC; ++o)
+        for (int o = 0; o < NOC; ++o)
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[o][j] = 0.f;
+            for (int j = 0; j < 16; ++j) acc[o][j] = 0.f;
 
-    const int NCr = g.nc;  // 16-row chunks per term: ceil((BY + 2r) / 16) <= 8
-    const int S = K * NCr;
-    uint32_t ph1 = 0, ph2 = 0;
-    int pend_oc = -1, pend_sfirst = 0;
-    bool timed_out = false;
+        const int NCr = g.nc;  // 16-row chunks per term: ceil((BY + 2r) / 16) <= 8
+        const int S = K * NCr;
+        int pend_oc = -1, pend_sfirst = 0;
+        const int kgring = g.Kw >> 3;
 
-    // A: channels of flat step s into A1[s & 1] (compute warps)
-    auto stage_A = [&](int s) {
-        const int k = s / NCr, c = s - k * NCr;
-        const float n0 = __ldg(nu_hi + 3 * k), n1 = __ldg(nu_hi + 3 * k + 1), n2 = __ldg(nu_hi + 3 * k + 2);
-        float f0[8], f1[8], f2[8];
-        const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24;
-        tmem_ld8(fa, f0);
-        tmem_ld8(fa + 8, f1);
-        tmem_ld8(fa + 16, f2);
-        tmem_wait_ld();
-        const uint32_t vm = (uint32_t)(vmask >> (8 * c)) & 0xFFu;
-        const int ry = 16 * c + row;
-        const bool centre_row = ry >= r && ry < r + BY && cmask;
-        uint32_t o[8][4];
-        float csv[8], snv[8];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            float cv[2], sv[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int j = 2 * p + e;
-                const float t = fmaf(n0, f0[j], fmaf(n1, f1[j], n2 * f2[j]));
-                const float fr = t - rintf(t);
-                float s_, c_;
-                __sincosf(6.28318530717958647692f * fr, &s_, &c_);
-                const bool v = (vm >> j) & 1u;
-                cv[e] = v ? c_ : 0.f;
-                sv[e] = v ? s_ : 0.f;
-                csv[j] = cv[e];
-                snv[j] = sv[e];
-            }
-            const typename P2::T hc = P2::make(cv[0], cv[1]);
-            const typename P2::T hs = P2::make(sv[0], sv[1]);
-            o[3][p] = bits(hc);
-            o[7][p] = bits(hs);
-            if constexpr (BF16) {
-                // BF16 keeps 8 mantissa bits: form the products in FP32 and round once
-                o[0][p] = bits(P2::make(cv[0] * f0[2 * p], cv[1] * f0[2 * p + 1]));
-                o[1][p] = bits(P2::make(cv[0] * f1[2 * p], cv[1] * f1[2 * p + 1]));
-                o[2][p] = bits(P2::make(cv[0] * f2[2 * p], cv[1] * f2[2 * p + 1]));
-                o[4][p] = bits(P2::make(sv[0] * f0[2 * p], sv[1] * f0[2 * p + 1]));
-                o[5][p] = bits(P2::make(sv[0] * f1[2 * p], sv[1] * f1[2 * p + 1]));
-                o[6][p] = bits(P2::make(sv[0] * f2[2 * p], sv[1] * f2[2 * p + 1]));
-            } else {
-                // FP16 (11-bit mantissa): packed half2 products of rounded operands
-                const typename P2::T g0 = P2::make(f0[2 * p], f0[2 * p + 1]);
-                const typename P2::T g1 = P2::make(f1[2 * p], f1[2 * p + 1]);
-                const typename P2::T g2 = P2::make(f2[2 * p], f2[2 * p + 1]);
-                o[0][p] = bits(__hmul2(hc, g0));
-                o[1][p] = bits(__hmul2(hc, g1));
-                o[2][p] = bits(__hmul2(hc, g2));
-                o[4][p] = bits(__hmul2(hs, g0));
-                o[5][p] = bits(__hmul2(hs, g1));
-                o[6][p] = bits(__hmul2(hs, g2));
-            }
-        }
-        if (centre_row) {  // centre cos/sin for the combine, slot = flat region row mod 128
-            const int slot = (16 * s + row) % g.ringC;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                if ((cmask >> j) & 1u) ring[ring_idx(slot, 8 * xg + j - r)] = make_float2(csv[j], snv[j]);
-        }
-        uint8_t *dst = A1 + (s & 1) * 32768 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048;
-#pragma unroll
-        for (int ch = 0; ch < 8; ++ch)
-            *reinterpret_cast<uint4 *>(dst + ch * 4096) = make_uint4(o[ch][0], o[ch][1], o[ch][2], o[ch][3]);
-    };
-
-    // C: combine output chunk oc (its window starts at flat step s_first)
-    auto stage_C = [&](int oc, int s_first) {
-        float vc[16], vs[16];
-        tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h), vc);
-        tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h + 1), vs);
-        tmem_wait_ld();
-        const int x = 32 * h + l;
-        int slot = (16 * s_first + r) % g.ringC;  // flat region row of output row 16 oc
-#pragma unroll
-        for (int o = 0; o < NOC; ++o) {
-            if (o == oc) {
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float2 cs = ring[ring_idx(slot, x)];
-                    if (++slot == g.ringC) slot = 0;
-                    acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
+        auto stage_A = [&](int s) {
+            const int k = s / NCr, c = s - k * NCr;
+            const float n0 = __ldg(nu_hi + 3 * k), n1 = __ldg(nu_hi + 3 * k + 1), n2 = __ldg(nu_hi + 3 * k + 2);
+            float f0[8], f1[8], f2[8];
+            const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24;
+            tmem_ld8(fa, f0);
+            tmem_ld8(fa + 8, f1);
+            tmem_ld8(fa + 16, f2);
+            tmem_wait_ld();
+            const uint32_t vm = (uint32_t)(vmask >> (8 * c)) & 0xFFu;
+            const int ry = 16 * c + row;
+            const bool centre_row = ry >= r && ry < r + BY && cmask;
+            uint32_t o[8][4];
+            float csv[8], snv[8];
+    #pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                float cv[2], sv[2];
+    #pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = 2 * p + e;
+                    const float t = fmaf(n0, f0[j], fmaf(n1, f1[j], n2 * f2[j]));
+                    const float fr = t - rintf(t);
+                    float s_, c_;
+                    __sincosf(6.28318530717958647692f * fr, &s_, &c_);
+                    const bool v = (vm >> j) & 1u;
+                    cv[e] = v ? c_ : 0.f;
+                    sv[e] = v ? s_ : 0.f;
+                    csv[j] = cv[e];
+                    snv[j] = sv[e];
+                }
+                const typename P2::T hc = P2::make(cv[0], cv[1]);
+                const typename P2::T hs = P2::make(sv[0], sv[1]);
+                o[3][p] = bits(hc);
+                o[7][p] = bits(hs);
+                if constexpr (BF16) {
+                    // BF16 keeps 8 mantissa bits: form the products in FP32 and round once
+                    o[0][p] = bits(P2::make(cv[0] * f0[2 * p], cv[1] * f0[2 * p + 1]));
+                    o[1][p] = bits(P2::make(cv[0] * f1[2 * p], cv[1] * f1[2 * p + 1]));
+                    o[2][p] = bits(P2::make(cv[0] * f2[2 * p], cv[1] * f2[2 * p + 1]));
+                    o[4][p] = bits(P2::make(sv[0] * f0[2 * p], sv[1] * f0[2 * p + 1]));
+                    o[5][p] = bits(P2::make(sv[0] * f1[2 * p], sv[1] * f1[2 * p + 1]));
+                    o[6][p] = bits(P2::make(sv[0] * f2[2 * p], sv[1] * f2[2 * p + 1]));
+                } else {
+                    // FP16 (11-bit mantissa): packed half2 products of rounded operands
+                    const typename P2::T g0 = P2::make(f0[2 * p], f0[2 * p + 1]);
+                    const typename P2::T g1 = P2::make(f1[2 * p], f1[2 * p + 1]);
+                    const typename P2::T g2 = P2::make(f2[2 * p], f2[2 * p + 1]);
+                    o[0][p] = bits(__hmul2(hc, g0));
+                    o[1][p] = bits(__hmul2(hc, g1));
+                    o[2][p] = bits(__hmul2(hc, g2));
+                    o[4][p] = bits(__hmul2(hs, g0));
+                    o[5][p] = bits(__hmul2(hs, g1));
+                    o[6][p] = bits(__hmul2(hs, g2));
                 }
             }
-        }
-    };
-
-    // X: D1 of flat step s -> A2 ring
-    auto stage_X = [&](int s) {
-        float v[32];
-        const uint32_t da = tmem + lane_base + kColD1 + 32 * h;
-        tmem_ld16(da, v);
-        tmem_ld16(da + 16, v + 16);
-        tmem_wait_ld();
-        const int ch = 2 * q + (l >> 4), gsel = ch >> 2, p = ch & 3;
-        const int kr = (16 * s + row) % g.Kw;
-        uint8_t *base = A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint4 pk = make_uint4(bits(P2::make(v[8 * i], v[8 * i + 1])), bits(P2::make(v[8 * i + 2], v[8 * i + 3])),
-                                        bits(P2::make(v[8 * i + 4], v[8 * i + 5])),
-                                        bits(P2::make(v[8 * i + 6], v[8 * i + 7])));
-            *reinterpret_cast<uint4 *>(base + i * 128) = pk;
-        }
-    };
-
-    // MMA issue (warp 8, lane 0).  Descriptors are built once; operand offsets
-    // are added to the 14-bit start-address field (address >> 4).
-    const uint64_t dA1 = sdesc(smem_u32(A1), 128, 2048);   // K-major: LBO = next K group, SBO = next 8 rows
-    const uint64_t dB1 = sdesc(smem_u32(B1), 1024, 128);
-    const uint64_t dA2 = sdesc(smem_u32(A2), 8192, 128);   // MN-major: LBO = next K group, SBO = next 8 columns
-    const uint64_t dB2 = sdesc(smem_u32(B2), 256, 128);
-    const uint32_t id1 = idesc(BF16 ? 1u : 0u, 0u, 64u);
-    const uint32_t id2 = idesc(BF16 ? 1u : 0u, 1u, 16u);
-    const int kgring = g.Kw >> 3;
-    auto issue_M1 = [&](int s) {
-        const uint64_t a = dA1 + (uint64_t)((s & 1) * (32768 >> 4));
-#pragma unroll
-        for (int ks = 0; ks < 8; ++ks)
-            if (ks < g.ks1) mma_f16(tmem + kColD1, a + 16 * ks, dB1 + 128 * ks, id1, ks > 0);
-        mma_commit(&mbar[0]);
-    };
-    auto issue_M2 = [&](int s_first, int t) {  // M-tile t of the vertical pass
-        const int kgb = (2 * s_first) % kgring;
-#pragma unroll
-        for (int ks = 0; ks < 5; ++ks)
-            if (ks < g.ksteps) {
-                int kg0 = kgb + 2 * ks;
-                if (kg0 >= kgring) kg0 -= kgring;
-                mma_f16(tmem + kColD2 + 16 * t, dA2 + (uint64_t)((kg0 * 8192 + t * 2048) >> 4), dB2 + 32 * ks, id2,
-                        ks > 0);
+            if (centre_row) {  // centre cos/sin for the combine, slot = flat region row mod 128
+                const int slot = (16 * s + row) % g.ringC;
+    #pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if ((cmask >> j) & 1u) ring[ring_idx(slot, 8 * xg + j - r)] = make_float2(csv[j], snv[j]);
             }
-        mma_commit(&mbar[1]);
-    };
+            uint8_t *dst = A1 + (s & 1) * 32768 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048;
+    #pragma unroll
+            for (int ch = 0; ch < 8; ++ch)
+                *reinterpret_cast<uint4 *>(dst + ch * 4096) = make_uint4(o[ch][0], o[ch][1], o[ch][2], o[ch][3]);
+        };
 
-    // ---- prologue ------------------------------------------------------------------
-    stage_A(0);
-    fence_async_smem();
-    __syncthreads();
-    if (w == 0 && l == 0) {
-        fence_after();
-        issue_M1(0);
-    }
+        // C: combine output chunk oc (its window starts at flat step s_first)
+        auto stage_C = [&](int oc, int s_first) {
+            float vc[16], vs[16];
+            tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h), vc);
+            tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h + 1), vs);
+            tmem_wait_ld();
+            const int x = 32 * h + l;
+            int slot = (16 * s_first + r) % g.ringC;  // flat region row of output row 16 oc
+    #pragma unroll
+            for (int o = 0; o < NOC; ++o) {
+                if (o == oc) {
+    #pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float2 cs = ring[ring_idx(slot, x)];
+                        if (++slot == g.ringC) slot = 0;
+                        acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
+                    }
+                }
+            }
+        };
 
-    // ---- pipeline ----------------------------------------------------------------------
-    for (int s = 0, c = 0; s < S; ++s, c = (c + 1 == NCr) ? 0 : c + 1) {
-        const int oc = c - g.lag;
-        const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
-        if (s + 1 < S) stage_A(s + 1);
+        // X: D1 of flat step s -> A2 ring
+        auto stage_X = [&](int s) {
+            float v[32];
+            const uint32_t da = tmem + lane_base + kColD1 + 32 * h;
+            tmem_ld16(da, v);
+            tmem_ld16(da + 16, v + 16);
+            tmem_wait_ld();
+            const int ch = 2 * q + (l >> 4), gsel = ch >> 2, p = ch & 3;
+            const int kr = (16 * s + row) % g.Kw;
+            uint8_t *base = A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512;
+    #pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint4 pk = make_uint4(bits(P2::make(v[8 * i], v[8 * i + 1])), bits(P2::make(v[8 * i + 2], v[8 * i + 3])),
+                                            bits(P2::make(v[8 * i + 4], v[8 * i + 5])),
+                                            bits(P2::make(v[8 * i + 6], v[8 * i + 7])));
+                *reinterpret_cast<uint4 *>(base + i * 128) = pk;
+            }
+        };
+
+        // MMA issue.  Descriptors are built once per CTA; operand offsets are
+        // added to the 14-bit start-address field (address >> 4).
+        auto issue_M1 = [&](int s) {
+            const uint64_t a = dA1 + (uint64_t)((s & 1) * (32768 >> 4));
+    #pragma unroll
+            for (int ks = 0; ks < 8; ++ks)
+                if (ks < g.ks1) mma_f16(tmem + kColD1, a + 16 * ks, dB1 + 128 * ks, id1, ks > 0);
+            mma_commit(&mbar[0]);
+        };
+        auto issue_M2 = [&](int s_first, int t) {  // M-tile t of the vertical pass
+            const int kgb = (2 * s_first) % kgring;
+    #pragma unroll
+            for (int ks = 0; ks < 5; ++ks)
+                if (ks < g.ksteps) {
+                    int kg0 = kgb + 2 * ks;
+                    if (kg0 >= kgring) kg0 -= kgring;
+                    mma_f16(tmem + kColD2 + 16 * t, dA2 + (uint64_t)((kg0 * 8192 + t * 2048) >> 4), dB2 + 32 * ks, id2,
+                            ks > 0);
+                }
+            mma_commit(&mbar[1]);
+        };
+
+        // ---- prologue ------------------------------------------------------------------
+        stage_A(0);
+
+        // ---- prologue ------------------------------------------------------------------
+        stage_A(0);
+        fence_async_smem();
+        __syncthreads();
+        if (w == 0 && l == 0) {
+            fence_after();
+            issue_M1(0);
+        }
+
+        // ---- pipeline ----------------------------------------------------------------------
+        for (int s = 0, c = 0; s < S; ++s, c = (c + 1 == NCr) ? 0 : c + 1) {
+            const int oc = c - g.lag;
+            const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
+            if (s + 1 < S) stage_A(s + 1);
+            if (pend_oc >= 0) {
+                if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                ph2 ^= 1;
+                fence_after();
+                stage_C(pend_oc, pend_sfirst);
+                pend_oc = -1;
+            }
+            if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
+            ph1 ^= 1;
+            fence_after();
+            stage_X(s);
+            fence_before();
+            fence_async_smem();
+            if (timed_out) abort_s = 1;
+            __syncthreads();
+            if (abort_s) goto cleanup;
+            if (l == 0 && (w == 0 || (w >= 4 && do_m2))) {
+                fence_after();
+                if (w == 0) {
+                    if (s + 1 < S) issue_M1(s + 1);
+                } else {
+                    issue_M2(s - g.lag, w - 4);
+                }
+            }
+            __syncwarp();
+            if (do_m2) {
+                pend_oc = oc;
+                pend_sfirst = s - g.lag;
+            }
+        }
         if (pend_oc >= 0) {
             if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
             ph2 ^= 1;
             fence_after();
             stage_C(pend_oc, pend_sfirst);
-            pend_oc = -1;
         }
-        if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
-        ph1 ^= 1;
-        fence_after();
-        stage_X(s);
-        fence_before();
-        fence_async_smem();
         if (timed_out) abort_s = 1;
+        fence_before();
         __syncthreads();
         if (abort_s) goto cleanup;
-        if (l == 0 && (w == 0 || (w >= 4 && do_m2))) {
-            fence_after();
-            if (w == 0) {
-                if (s + 1 < S) issue_M1(s + 1);
-            } else {
-                issue_M2(s - g.lag, w - 4);
+
+        // ---- P / Z ----------------------------------------------------------------
+        {
+            float *zbuf = reinterpret_cast<float *>(sm + lay.offC);  // [BY][64], reuses the centre ring
+            const int x = 32 * h + l;
+            if (q == 3) {
+#pragma unroll
+                for (int o = 0; o < NOC; ++o)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (16 * o + j < BY) zbuf[(16 * o + j) * kBX + x] = acc[o][j];
+            }
+            __syncthreads();
+            const int gx = tx0 + x;
+            if (q < 3 && gx < W) {
+#pragma unroll
+                for (int o = 0; o < NOC; ++o)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int y = 16 * o + j, gy = ty0 + y;
+                        if (y < BY && gy < H)
+                            out[q * plane + (size_t)gy * pitch + gx] = acc[o][j] / zbuf[y * kBX + x];
+                    }
             }
         }
-        __syncwarp();
-        if (do_m2) {
-            pend_oc = oc;
-            pend_sfirst = s - g.lag;
-        }
-    }
-    if (pend_oc >= 0) {
-        if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
-        ph2 ^= 1;
+        fence_before();
+        __syncthreads();  // zbuf, ring and TMEM are reused by the next tile
         fence_after();
-        stage_C(pend_oc, pend_sfirst);
-    }
-    if (timed_out) abort_s = 1;
-    fence_before();
-    __syncthreads();
-    if (abort_s) goto cleanup;
-
-    // ---- P / Z ----------------------------------------------------------------
-    {
-        float *zbuf = reinterpret_cast<float *>(sm + g.offC);  // [BY][64], reuses the centre ring
-        const int x = 32 * h + l;
-        if (q == 3) {
-#pragma unroll
-            for (int o = 0; o < NOC; ++o)
-#pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (16 * o + j < BY) zbuf[(16 * o + j) * kBX + x] = acc[o][j];
-        }
-        __syncthreads();
-        const int gx = tx0 + x;
-        if (q < 3 && gx < W) {
-#pragma unroll
-            for (int o = 0; o < NOC; ++o)
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int y = 16 * o + j, gy = ty0 + y;
-                    if (y < BY && gy < H) out[q * plane + (size_t)gy * pitch + gx] = acc[o][j] / zbuf[y * kBX + x];
-                }
-        }
     }
 
 cleanup:
@@ -508,60 +555,126 @@ cleanup:
     if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
 
-template <int NOC, bool BF16>
-int launch_noc(const float *in, float *out, int H, int W, int pitch, const bf_plan_s &p, const TcGeom &g,
-               cudaStream_t s) {
-    auto kern = mcsf_tc_kernel<NOC, BF16>;
-    int dev = 0, max_smem = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if ((int)g.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem) != cudaSuccess) {
-        cudaGetLastError();
-        return BF_ERR_CUDA;
-    }
-    int *st = status_word(dev);
-    if (!st) return BF_ERR_NOMEM;
-    dim3 grid(cdiv(W, kBX), cdiv(H, g.BY));
-    kern<<<grid, kT, g.smem, s>>>(in, out, H, W, pitch, p.nu_hi, p.K, BF16 ? p.tapsbf : p.taps16, g, st);
-    return cuda_err(cudaGetLastError());
+// ---------------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------------
+
+// Per-image geometry for window radius r; false if the tile scheme cannot hold it.
+bool tc_geometry(int r, TcImg &g) {
+    g.r = r;
+    g.lag = cdiv(2 * r, 16);
+    g.Kw = 16 * (g.lag + 1);
+    g.ksteps = g.Kw / 16;
+    g.Kw1 = 16 * cdiv(kBX + 2 * r, 16);
+    g.ks1 = g.Kw1 / 16;
+    if (g.Kw1 > 128 || g.ksteps > 5) return false;
+    int noc = (128 - 2 * r) / 16;
+    if (noc > kNC - g.lag) noc = kNC - g.lag;
+    if (noc > kNOC) noc = kNOC;
+    if (noc < 1) return false;
+    g.BY = 16 * noc;
+    g.nc = cdiv(g.BY + 2 * r, 16);
+    g.ringC = 16 * (g.lag + 3);  // rows written ahead by stage A never reach the rows stage C reads
+    return true;
+}
+
+TcLayout tc_layout(int max_Kw, int max_Kw1, int max_ringC, int max_BY) {
+    TcLayout L{};
+    L.offA2 = 65536;
+    L.offB1 = L.offA2 + (uint32_t)(max_Kw / 8) * 8192;
+    L.offB = L.offB1 + (uint32_t)max_Kw1 * 128;
+    L.offC = (L.offB + (uint32_t)max_Kw * 32 + 127) & ~127u;
+    const uint32_t ring_bytes = (uint32_t)max_ringC * kBX * 8;
+    const uint32_t z_bytes = (uint32_t)max_BY * kBX * 4;
+    L.smem = L.offC + (ring_bytes > z_bytes ? ring_bytes : z_bytes);
+    if (L.smem < 120 * 1024) L.smem = 120 * 1024;  // one CTA per SM: it holds all 512 TMEM columns
+    return L;
 }
 
 }  // namespace
 
+// Builds the image table (images ordered by per-tile cost, largest first, so
+// the dynamic queue ends on cheap tiles), copies it with zeroed control words
+// into `scratch`, and launches one persistent grid.  `scratch` must hold
+// tc_scratch_bytes(n) bytes and is owned by the caller for the stream.
+size_t tc_scratch_bytes(int n) { return (size_t)kCtrlWords * sizeof(int) + (size_t)n * sizeof(TcImg); }
+
+int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s) {
+    if (n <= 0) return BF_OK;
+    std::vector<TcImg> tab;
+    tab.reserve(n);
+    std::vector<long long> cost;
+    int max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16;
+    for (int i = 0; i < n; ++i) {
+        const bf_item &it = items[i];
+        const bf_plan_s &p = *it.plan;
+        if (it.H == 0 || it.W == 0) continue;
+        if (p.d != 3) return BF_ERR_UNSUPPORTED;
+        TcImg g{};
+        if (!tc_geometry(p.r, g)) return BF_ERR_UNSUPPORTED;
+        g.in = it.in;
+        g.out = it.out;
+        g.nu_hi = p.nu_hi;
+        g.taps = variant == BF_BF16TC ? p.tapsbf : p.taps16;
+        g.H = it.H;
+        g.W = it.W;
+        g.pitch = it.pitch;
+        g.K = p.K;
+        g.tiles_x = cdiv(it.W, kBX);
+        max_Kw = std::max(max_Kw, g.Kw);
+        max_Kw1 = std::max(max_Kw1, g.Kw1);
+        max_ringC = std::max(max_ringC, g.ringC);
+        max_BY = std::max(max_BY, g.BY);
+        tab.push_back(g);
+        cost.push_back((long long)g.K * g.nc);
+    }
+    if (tab.empty()) return BF_OK;
+    std::vector<int> order(tab.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (cost[a] != cost[b]) return cost[a] > cost[b];
+        return tab[a].r < tab[b].r;
+    });
+    std::vector<unsigned char> host(tc_scratch_bytes((int)tab.size()), 0);
+    TcImg *dst = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
+    int total = 0;
+    for (size_t i = 0; i < order.size(); ++i) {
+        TcImg g = tab[order[i]];
+        g.tile_begin = total;
+        total += g.tiles_x * cdiv(g.H, g.BY);
+        dst[i] = g;
+    }
+    const TcLayout lay = tc_layout(max_Kw, max_Kw1, max_ringC, max_BY);
+    int dev = 0, max_smem = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if ((int)lay.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
+    auto kern = variant == BF_BF16TC ? mcsf_tc_kernel<true> : mcsf_tc_kernel<false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(scratch, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
+    const int grid = std::min(total, nsm);
+    int *ctrl = reinterpret_cast<int *>(scratch);
+    const TcImg *imgs = reinterpret_cast<const TcImg *>(reinterpret_cast<char *>(scratch) + kCtrlWords * sizeof(int));
+    kern<<<grid, kT, lay.smem, s>>>(imgs, (int)tab.size(), total, ctrl, status, lay);
+    return cuda_err(cudaGetLastError());
+}
+
 int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int variant,
               cudaStream_t s) {
-    if (p.d != 3) return BF_ERR_UNSUPPORTED;
-    TcGeom g{};
-    g.r = p.r;
-    g.lag = cdiv(2 * p.r, 16);
-    g.Kw = 16 * (g.lag + 1);
-    g.ksteps = g.Kw / 16;
-    g.Kw1 = 16 * cdiv(kBX + 2 * p.r, 16);
-    g.ks1 = g.Kw1 / 16;
-    if (g.Kw1 > 128 || g.ksteps > 5) return BF_ERR_UNSUPPORTED;
-    int noc = (128 - 2 * p.r) / 16;
-    if (noc > kNC - g.lag) noc = kNC - g.lag;
-    if (noc > 5) noc = 5;
-    if (noc < 4) return BF_ERR_UNSUPPORTED;
-    g.BY = 16 * noc;
-    g.nc = cdiv(g.BY + 2 * p.r, 16);
-    g.ringC = 16 * (g.lag + 3);  // rows written ahead by stage A never reach the rows stage C reads
-    g.offA2 = 65536;
-    g.offB1 = g.offA2 + (uint32_t)(g.Kw / 8) * 8192;
-    g.offB = g.offB1 + (uint32_t)g.Kw1 * 128;
-    g.offC = g.offB + (uint32_t)g.Kw * 32;
-    g.offC = (g.offC + 127) & ~127u;
-    const uint32_t ring_bytes = (uint32_t)g.ringC * kBX * 8;
-    const uint32_t z_bytes = (uint32_t)g.BY * kBX * 4;
-    g.smem = g.offC + (ring_bytes > z_bytes ? ring_bytes : z_bytes);
-    if (g.smem < 120 * 1024) g.smem = 120 * 1024;  // one CTA per SM: it holds all 512 TMEM columns
-    const bool bf = variant == BF_BF16TC;
-    switch (noc) {
-        case 4: return bf ? launch_noc<4, true>(in, out, H, W, pitch, p, g, s) : launch_noc<4, false>(in, out, H, W, pitch, p, g, s);
-        case 5: return bf ? launch_noc<5, true>(in, out, H, W, pitch, p, g, s) : launch_noc<5, false>(in, out, H, W, pitch, p, g, s);
-        default: return BF_ERR_UNSUPPORTED;
-    }
+    bf_item it{const_cast<bf_plan_s *>(&p), in, out, H, W, pitch};
+    void *scratch = stream_scratch(s, tc_scratch_bytes(1));
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int *st = status_word(dev);
+    if (!scratch || !st) return BF_ERR_NOMEM;
+    return tc_launch_batch(&it, 1, variant, scratch, st, s);
 }
 
 }  // namespace bf
