@@ -142,6 +142,40 @@ typedef struct {
 int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
 
 /*
+ * bf_filter_batch_noalloc -- bf_filter_batch for the tensor-core variants that
+ * allocates nothing.  The paper has no counterpart: this is a service of the
+ * library, not a step of the method.
+ *
+ * bf_filter_batch and bf_filter keep their tile counter and image table in
+ * device scratch that the library allocates (cudaMalloc) the first time a
+ * stream needs it, or when a larger batch arrives.  Some callers cannot let a
+ * library allocate: applications whose device memory is handed out entirely
+ * by their own allocator (a framework's caching allocator, a fixed pool sized
+ * at start-up), where a foreign cudaMalloc can fail or fragment the pool, and
+ * latency-critical loops that cannot absorb the device-wide synchronisation a
+ * cudaMalloc or cudaFree may cause.  This entry point serves them: its
+ * scratch is a file-scope device array of 24.25 KB (the control words plus
+ * the table for BF_NOALLOC_MAX_ITEMS images) that every GPU loading the
+ * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
+ * other allocating routine, on the device or the host.
+ *   items, stream   as bf_filter_batch; the caller still owns every image.
+ *   variant         BF_FP16TC or BF_BF16TC (else BF_ERR_ARG); every image
+ *                   must have d = 3 (else BF_ERR_UNSUPPORTED).
+ *   n               0..BF_NOALLOC_MAX_ITEMS; larger n returns BF_ERR_BUDGET
+ *                   before any work is queued (split the batch).
+ * Results are identical to bf_filter_batch with the same arguments.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current) and caches it; make that
+ * first call before any stream capture.  All calls share the one array and
+ * it keeps the last call's contents: each call resets the tile counter and
+ * rewrites the table, so calls whose work overlaps on the GPU (on different
+ * streams, or from several host threads) race and must be serialised by the
+ * caller.  Timeouts recorded by its kernel are reported by bf_last_status.
+ */
+#define BF_NOALLOC_MAX_ITEMS 256
+int bf_filter_batch_noalloc(const bf_item *items, int n, int variant, void *stream);
+
+/*
  * bf_filter_host -- end-to-end convenience call for callers holding host
  * images: copies `in_host` (planar [d][H][W], pitch W) to library-owned
  * device buffers, filters, copies the result to `out_host`, and synchronises

@@ -32,6 +32,7 @@ BF_MAX_D = 8
 BF_MAX_RADIUS = 32
 BF_MAX_N = 4096
 BF_MAX_K = 65536
+BF_NOALLOC_MAX_ITEMS = 256
 
 BF_FP32 = 0
 BF_FP16TC = 1
@@ -81,6 +82,7 @@ def _load():
         lib.bf_plan_destroy.argtypes = [vp]
         lib.bf_filter.argtypes = [vp, vp, vp, i, i, i, i, vp]
         lib.bf_filter_batch.argtypes = [ctypes.POINTER(bf_item), i, i, vp]
+        lib.bf_filter_batch_noalloc.argtypes = [ctypes.POINTER(bf_item), i, i, vp]
         lib.bf_filter_host.argtypes = [vp, vp, vp, i, i, i, vp]
         lib.bf_last_status.argtypes = [vp]
         lib.bf_error_string.argtypes = [i]
@@ -173,6 +175,16 @@ def bf_filter_batch(items, variant: int = BF_FP32, stream: int = 0):
         arr[k] = bf_item(plan.handle, ip, op, H, W, pitch)
         keep.append(plan)
     _check(_load().bf_filter_batch(arr, len(items), int(variant), ctypes.c_void_p(stream)), "bf_filter_batch")
+
+
+def bf_filter_batch_noalloc(items, variant: int = BF_FP16TC, stream: int = 0):
+    """As bf_filter_batch for the tensor-core variants, without any allocation
+    (scratch in a static device array; at most BF_NOALLOC_MAX_ITEMS images)."""
+    arr = (bf_item * max(1, len(items)))()
+    for k, (plan, ip, op, H, W, pitch) in enumerate(items):
+        arr[k] = bf_item(plan.handle, ip, op, H, W, pitch)
+    _check(_load().bf_filter_batch_noalloc(arr, len(items), int(variant), ctypes.c_void_p(stream)),
+           "bf_filter_batch_noalloc")
 
 
 def bf_filter_host(plan: Plan, in_host: np.ndarray, out_host: np.ndarray | None = None, variant: int = BF_FP32,

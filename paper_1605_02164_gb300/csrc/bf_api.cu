@@ -16,6 +16,7 @@ std::mutex g_status_mu;
 int *g_status[64] = {nullptr};
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
 
 int check_image_args(const bf_plan_s *p, const float *in, const float *out, int H, int W, int pitch) {
     if (!p) return BF_ERR_ARG;
@@ -29,7 +30,6 @@ int check_image_args(const bf_plan_s *p, const float *in, const float *out, int 
     if (a < b + bytes && b < a + bytes) return BF_ERR_ARG;  // overlap
     return BF_OK;
 }
-}  // namespace
 
 void *stream_scratch(cudaStream_t stream, size_t bytes) {
     struct Slot {
@@ -181,7 +181,8 @@ extern "C" int bf_last_status(void *stream) {
     int v = 0;
     if (cudaMemcpy(&v, w, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BF_ERR_CUDA;
     if (v != 0) cudaMemset(w, 0, sizeof(int));
-    return v;
+    const int v2 = bf::noalloc_take_status();  // the allocation-free entry point keeps its own word
+    return v != 0 ? v : v2;
 }
 
 extern "C" const char *bf_error_string(int code) {

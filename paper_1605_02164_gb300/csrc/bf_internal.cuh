@@ -35,6 +35,11 @@ constexpr uint32_t kPlanMagic = 0xBF1605u;
 
 // Status word: one per device, written by device guards, read by bf_last_status.
 int *status_word(int device);
+// Status word of bf_filter_batch_noalloc on the current device (cleared when read).
+int noalloc_take_status();
+
+// Host-side checks shared by the image entry points (BF_OK or a BF_ERR_* code).
+int check_image_args(const bf_plan_s *p, const float *in, const float *out, int H, int W, int pitch);
 
 // FP32 fused kernel (csrc/bf_fp32.cu).
 int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s);

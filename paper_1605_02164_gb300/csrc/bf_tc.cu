@@ -29,6 +29,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "bf_internal.cuh"
@@ -599,52 +600,45 @@ TcLayout tc_layout(int max_Kw, int max_Kw1, int max_ringC, int max_BY) {
 // tc_scratch_bytes(n) bytes and is owned by the caller for the stream.
 size_t tc_scratch_bytes(int n) { return (size_t)kCtrlWords * sizeof(int) + (size_t)n * sizeof(TcImg); }
 
-int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s) {
-    if (n <= 0) return BF_OK;
-    std::vector<TcImg> tab;
-    tab.reserve(n);
-    std::vector<long long> cost;
-    int max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16;
-    for (int i = 0; i < n; ++i) {
-        const bf_item &it = items[i];
-        const bf_plan_s &p = *it.plan;
-        if (it.H == 0 || it.W == 0) continue;
-        if (p.d != 3) return BF_ERR_UNSUPPORTED;
-        TcImg g{};
-        if (!tc_geometry(p.r, g)) return BF_ERR_UNSUPPORTED;
-        g.in = it.in;
-        g.out = it.out;
-        g.nu_hi = p.nu_hi;
-        g.taps = variant == BF_BF16TC ? p.tapsbf : p.taps16;
-        g.H = it.H;
-        g.W = it.W;
-        g.pitch = it.pitch;
-        g.K = p.K;
-        g.tiles_x = cdiv(it.W, kBX);
-        max_Kw = std::max(max_Kw, g.Kw);
-        max_Kw1 = std::max(max_Kw1, g.Kw1);
-        max_ringC = std::max(max_ringC, g.ringC);
-        max_BY = std::max(max_BY, g.BY);
-        tab.push_back(g);
-        cost.push_back((long long)g.K * g.nc);
+namespace {
+
+// Descriptor of one image (tile_begin left 0); false if the tile scheme cannot hold it.
+int tc_fill(const bf_item &it, int variant, TcImg &g) {
+    const bf_plan_s &p = *it.plan;
+    if (p.d != 3) return BF_ERR_UNSUPPORTED;
+    g = TcImg{};
+    if (!tc_geometry(p.r, g)) return BF_ERR_UNSUPPORTED;
+    g.in = it.in;
+    g.out = it.out;
+    g.nu_hi = p.nu_hi;
+    g.taps = variant == BF_BF16TC ? p.tapsbf : p.taps16;
+    g.H = it.H;
+    g.W = it.W;
+    g.pitch = it.pitch;
+    g.K = p.K;
+    g.tiles_x = cdiv(it.W, kBX);
+    return BF_OK;
+}
+
+// Tile offsets and the shared-memory layout of an ordered table.
+void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
+    int max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16, t = 0;
+    for (int i = 0; i < m; ++i) {
+        tab[i].tile_begin = t;
+        t += tab[i].tiles_x * cdiv(tab[i].H, tab[i].BY);
+        max_Kw = std::max(max_Kw, tab[i].Kw);
+        max_Kw1 = std::max(max_Kw1, tab[i].Kw1);
+        max_ringC = std::max(max_ringC, tab[i].ringC);
+        max_BY = std::max(max_BY, tab[i].BY);
     }
-    if (tab.empty()) return BF_OK;
-    std::vector<int> order(tab.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        if (cost[a] != cost[b]) return cost[a] > cost[b];
-        return tab[a].r < tab[b].r;
-    });
-    std::vector<unsigned char> host(tc_scratch_bytes((int)tab.size()), 0);
-    TcImg *dst = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
-    int total = 0;
-    for (size_t i = 0; i < order.size(); ++i) {
-        TcImg g = tab[order[i]];
-        g.tile_begin = total;
-        total += g.tiles_x * cdiv(g.H, g.BY);
-        dst[i] = g;
-    }
-    const TcLayout lay = tc_layout(max_Kw, max_Kw1, max_ringC, max_BY);
+    *total = t;
+    *lay = tc_layout(max_Kw, max_Kw1, max_ringC, max_BY);
+}
+
+// Launch over a table already in device memory.  The table is ordered by
+// per-tile cost (largest first) so the dynamic queue ends on cheap tiles.
+int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *status_dev, const TcLayout &lay,
+              int variant, cudaStream_t s) {
     int dev = 0, max_smem = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -655,16 +649,147 @@ int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int
         cudaGetLastError();
         return BF_ERR_CUDA;
     }
-    if (cudaMemcpyAsync(scratch, host.data(), host.size(), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    kern<<<std::min(total, nsm), kT, lay.smem, s>>>(imgs_dev, m, total, ctrl_dev, status_dev, lay);
+    return cuda_err(cudaGetLastError());
+}
+
+bool cost_before(const TcImg &a, const TcImg &b) {
+    const long long ca = (long long)a.K * a.nc, cb = (long long)b.K * b.nc;
+    if (ca != cb) return ca > cb;
+    return a.r < b.r;
+}
+
+}  // namespace
+
+int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s) {
+    if (n <= 0) return BF_OK;
+    std::vector<unsigned char> host(tc_scratch_bytes(n), 0);  // control words (zero) + table
+    TcImg *tab = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (items[i].H == 0 || items[i].W == 0) continue;
+        const int rc = tc_fill(items[i], variant, tab[m]);
+        if (rc != BF_OK) return rc;
+        ++m;
+    }
+    if (m == 0) return BF_OK;
+    std::stable_sort(tab, tab + m, cost_before);
+    int total = 0;
+    TcLayout lay{};
+    tc_finish(tab, m, &total, &lay);
+    const size_t bytes = (size_t)kCtrlWords * sizeof(int) + (size_t)m * sizeof(TcImg);
+    if (cudaMemcpyAsync(scratch, host.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         cudaGetLastError();
         return BF_ERR_CUDA;
     }
-    const int grid = std::min(total, nsm);
     int *ctrl = reinterpret_cast<int *>(scratch);
     const TcImg *imgs = reinterpret_cast<const TcImg *>(reinterpret_cast<char *>(scratch) + kCtrlWords * sizeof(int));
-    kern<<<grid, kT, lay.smem, s>>>(imgs, (int)tab.size(), total, ctrl, status, lay);
-    return cuda_err(cudaGetLastError());
+    return tc_launch(imgs, m, total, ctrl, status, lay, variant, s);
 }
+
+// ---------------------------------------------------------------------------------
+// Allocation-free entry point
+// ---------------------------------------------------------------------------------
+
+// Scratch of bf_filter_batch_noalloc: control words (tile counter, status)
+// followed by the image table for at most BF_NOALLOC_MAX_ITEMS images.  Every
+// GPU that loads the library holds these 24.25 KB until the process exits.
+constexpr size_t kNoAllocBytes = (size_t)kCtrlWords * sizeof(int) + (size_t)BF_NOALLOC_MAX_ITEMS * sizeof(TcImg);
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+void *noalloc_scratch(int dev) {
+    if (dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_ptr[dev] = ptr;
+    }
+    return g_noalloc_ptr[dev];
+}
+}  // namespace
+
+// Status word of the allocation-free entry point on the current device, or
+// BF_OK if it was never used there; cleared when non-zero.
+int noalloc_take_status() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return BF_OK;
+    void *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        p = g_noalloc_ptr[dev];
+    }
+    if (!p) return BF_OK;
+    int v = 0;
+    int *st = reinterpret_cast<int *>(p) + 1;
+    if (cudaMemcpy(&v, st, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BF_ERR_CUDA;
+    if (v != 0) {
+        const int zero = 0;
+        cudaMemcpy(st, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    }
+    return v;
+}
+
+}  // namespace bf
+
+extern "C" int bf_filter_batch_noalloc(const bf_item *items, int n, int variant, void *stream) {
+    using namespace bf;
+    if (n < 0 || (n > 0 && !items)) return BF_ERR_ARG;
+    if (variant != BF_FP16TC && variant != BF_BF16TC) return BF_ERR_ARG;
+    if (n > BF_NOALLOC_MAX_ITEMS) return BF_ERR_BUDGET;
+    for (int i = 0; i < n; ++i) {
+        const int rc = check_image_args(items[i].plan, items[i].in, items[i].out, items[i].H, items[i].W,
+                                        items[i].pitch);
+        if (rc != BF_OK) return rc;
+    }
+    TcImg tab[BF_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap allocation either
+    int m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (items[i].H == 0 || items[i].W == 0) continue;
+        const int rc = tc_fill(items[i], variant, tab[m]);
+        if (rc != BF_OK) return rc;
+        ++m;
+    }
+    if (m == 0) return BF_OK;
+    for (int a = 1; a < m; ++a) {  // stable insertion sort by cost (no temporary buffer)
+        const TcImg t = tab[a];
+        int b = a - 1;
+        while (b >= 0 && cost_before(t, tab[b])) {
+            tab[b + 1] = tab[b];
+            --b;
+        }
+        tab[b + 1] = t;
+    }
+    int total = 0;
+    TcLayout lay{};
+    tc_finish(tab, m, &total, &lay);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BF_ERR_CUDA;
+    char *scr = reinterpret_cast<char *>(noalloc_scratch(dev));
+    if (!scr) return BF_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    int *ctrl = reinterpret_cast<int *>(scr);
+    TcImg *imgs = reinterpret_cast<TcImg *>(scr + kCtrlWords * sizeof(int));
+    const int zero = 0;  // the tile counter must start at zero; the status word is left as is
+    if (cudaMemcpyAsync(ctrl, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(imgs, tab, (size_t)m * sizeof(TcImg), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
+    return tc_launch(imgs, m, total, ctrl, ctrl + 1, lay, variant, s);
+}
+
+namespace bf {
 
 int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int variant,
               cudaStream_t s) {
