@@ -17,6 +17,10 @@
 // Both passes are register-blocked: a thread produces 8 consecutive outputs
 // from a sliding 16-value register window, 8 taps per step (taps past 2r are
 // zero).  HBM sees the input once per term through L2 and the output once.
+// When the 2(d+1) channels of a chunk do not fit in shared memory (large d
+// and r), each term runs in two passes (G = 2): the cos-group channels
+// cos f_c, cos and then the sin-group channels sin f_c, sin, each pass adding
+// its half of P and Z (cos/sin are recomputed in the second pass).
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -36,10 +40,10 @@ struct Geom {
 
 __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
-template <int D>
+template <int D, int G>
 Geom make_geom(int r, int BY) {
     Geom g;
-    constexpr int NCH = 2 * (D + 1);
+    constexpr int NCH = 2 * (D + 1) / G;  // channels held per pass
     g.r = r;
     g.BY = BY;
     g.RX = kBX + 2 * r;
@@ -56,12 +60,12 @@ Geom make_geom(int r, int BY) {
     return g;
 }
 
-template <int D>
+template <int D, int G>
 __global__ void __launch_bounds__(kThreads, 1)
     mcsf_fp32_kernel(const float *__restrict__ in, float *__restrict__ out, int H, int W, int pitch,
                      const float *__restrict__ nu_hi, const float *__restrict__ nu_lo, int K,
                      const float *__restrict__ taps_g, Geom g) {
-    constexpr int NCH = 2 * (D + 1);
+    constexpr int NCH = 2 * (D + 1) / G;  // channels held per pass
     extern __shared__ __align__(16) float smem[];
     float *taps = smem;                                   // [TP]
     float *CH = taps + g.TP;                              // [NCH][kRC][RXP]
@@ -87,6 +91,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             nh[c] = __ldg(nu_hi + k * D + c);
             nl[c] = __ldg(nu_lo + k * D + c);
         }
+      for (int gi = 0; gi < G; ++gi) {  // channel group of this pass (G = 1: both groups at once)
         for (int j = 0; j < g.NJ; ++j) {
             // ---------------- A: phases, cos/sin, modulated channels ----------
             const int ring0 = (j * kRC) % g.RING;
@@ -117,13 +122,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         sincospif(2.f * __fadd_rn(tf, te), &sth, &cth);
                     }
                     float *dst = CH + row * g.RXP + col;
+                    if (G == 1) {
 #pragma unroll
-                    for (int c = 0; c < D; ++c) {
-                        dst[(size_t)c * kRC * g.RXP] = cth * fv[c];
-                        dst[(size_t)(D + 1 + c) * kRC * g.RXP] = sth * fv[c];
+                        for (int c = 0; c < D; ++c) {
+                            dst[(size_t)c * kRC * g.RXP] = cth * fv[c];
+                            dst[(size_t)(D + 1 + c) * kRC * g.RXP] = sth * fv[c];
+                        }
+                        dst[(size_t)D * kRC * g.RXP] = cth;
+                        dst[(size_t)(2 * D + 1) * kRC * g.RXP] = sth;
+                    } else {
+                        const float trig = gi == 0 ? cth : sth;
+#pragma unroll
+                        for (int c = 0; c < D; ++c) dst[(size_t)c * kRC * g.RXP] = trig * fv[c];
+                        dst[(size_t)D * kRC * g.RXP] = trig;
                     }
-                    dst[(size_t)D * kRC * g.RXP] = cth;
-                    dst[(size_t)(2 * D + 1) * kRC * g.RXP] = sth;
                     const int cx = col - r;
                     if (cx >= 0 && cx < kBX) CS[(cs0 + row) * kBX + cx] = make_float2(cth, sth);
                 }
@@ -161,53 +173,94 @@ __global__ void __launch_bounds__(kThreads, 1)
             // ---------------- C: vertical pass + combine ----------------------
             const int oc = j - g.lag;
             if (oc >= 0 && oc * kRC < BY) {
-                for (int task = tid; task < kBX * (D + 1) * 2; task += kThreads) {
-                    const int x = task & 31;
-                    const int rb = (task >> 5) & 1;
-                    const int p = task >> 6;
-                    const int o0 = oc * kRC + rb * 8;
-                    const float *hc = HB + p * kBX + x;            // cos-group channel p
-                    const float *hs = HB + (D + 1 + p) * kBX + x;  // sin-group channel p
-                    float vc[8], vs[8], wc[16], ws[16];
-                    int blk = o0 % g.RING;
-#pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        vc[m] = 0.f;
-                        vs[m] = 0.f;
-                        wc[m] = hc[(size_t)(blk + m) * g.HB_SLOT];
-                        ws[m] = hs[(size_t)(blk + m) * g.HB_SLOT];
-                    }
-                    for (int v0 = 0; v0 < g.TP; v0 += 8) {
-                        blk += 8;
-                        if (blk >= g.RING) blk -= g.RING;
-#pragma unroll
+                if (G == 1) {
+                    for (int task = tid; task < kBX * (D + 1) * 2; task += kThreads) {
+                        const int x = task & 31;
+                        const int rb = (task >> 5) & 1;
+                        const int p = task >> 6;
+                        const int o0 = oc * kRC + rb * 8;
+                        const float *hc = HB + p * kBX + x;            // cos-group channel p
+                        const float *hs = HB + (D + 1 + p) * kBX + x;  // sin-group channel p
+                        float vc[8], vs[8], wc[16], ws[16];
+                        int blk = o0 % g.RING;
+    #pragma unroll
                         for (int m = 0; m < 8; ++m) {
-                            wc[8 + m] = hc[(size_t)(blk + m) * g.HB_SLOT];
-                            ws[8 + m] = hs[(size_t)(blk + m) * g.HB_SLOT];
+                            vc[m] = 0.f;
+                            vs[m] = 0.f;
+                            wc[m] = hc[(size_t)(blk + m) * g.HB_SLOT];
+                            ws[m] = hs[(size_t)(blk + m) * g.HB_SLOT];
                         }
-                        const float4 ta = *reinterpret_cast<const float4 *>(taps + v0);
-                        const float4 tb = *reinterpret_cast<const float4 *>(taps + v0 + 4);
-                        const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
-#pragma unroll
-                        for (int vv = 0; vv < 8; ++vv)
-#pragma unroll
+                        for (int v0 = 0; v0 < g.TP; v0 += 8) {
+                            blk += 8;
+                            if (blk >= g.RING) blk -= g.RING;
+    #pragma unroll
                             for (int m = 0; m < 8; ++m) {
-                                vc[m] = fmaf(tv[vv], wc[m + vv], vc[m]);
-                                vs[m] = fmaf(tv[vv], ws[m + vv], vs[m]);
+                                wc[8 + m] = hc[(size_t)(blk + m) * g.HB_SLOT];
+                                ws[8 + m] = hs[(size_t)(blk + m) * g.HB_SLOT];
                             }
-#pragma unroll
+                            const float4 ta = *reinterpret_cast<const float4 *>(taps + v0);
+                            const float4 tb = *reinterpret_cast<const float4 *>(taps + v0 + 4);
+                            const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+    #pragma unroll
+                            for (int vv = 0; vv < 8; ++vv)
+    #pragma unroll
+                                for (int m = 0; m < 8; ++m) {
+                                    vc[m] = fmaf(tv[vv], wc[m + vv], vc[m]);
+                                    vs[m] = fmaf(tv[vv], ws[m + vv], vs[m]);
+                                }
+    #pragma unroll
+                            for (int m = 0; m < 8; ++m) {
+                                wc[m] = wc[m + 8];
+                                ws[m] = ws[m + 8];
+                            }
+                        }
+                        int crow = (o0 + r) % g.RING_CS;
+                        float *acc = ACC + ((size_t)p * BY + o0) * kBX + x;
+    #pragma unroll
                         for (int m = 0; m < 8; ++m) {
-                            wc[m] = wc[m + 8];
-                            ws[m] = ws[m + 8];
+                            const float2 cs = CS[crow * kBX + x];
+                            acc[m * kBX] += fmaf(cs.x, vc[m], cs.y * vs[m]);
+                            if (++crow == g.RING_CS) crow = 0;
                         }
                     }
-                    int crow = (o0 + r) % g.RING_CS;
-                    float *acc = ACC + ((size_t)p * BY + o0) * kBX + x;
+                } else {
+                    // one channel group: V = blur of (trig f_p or trig), acc += trig(centre) V
+                    for (int task = tid; task < kBX * (D + 1) * 2; task += kThreads) {
+                        const int x = task & 31;
+                        const int rb = (task >> 5) & 1;
+                        const int p = task >> 6;
+                        const int o0 = oc * kRC + rb * 8;
+                        const float *hc = HB + p * kBX + x;
+                        float vc[8], wc[16];
+                        int blk = o0 % g.RING;
 #pragma unroll
-                    for (int m = 0; m < 8; ++m) {
-                        const float2 cs = CS[crow * kBX + x];
-                        acc[m * kBX] += fmaf(cs.x, vc[m], cs.y * vs[m]);
-                        if (++crow == g.RING_CS) crow = 0;
+                        for (int m = 0; m < 8; ++m) {
+                            vc[m] = 0.f;
+                            wc[m] = hc[(size_t)(blk + m) * g.HB_SLOT];
+                        }
+                        for (int v0 = 0; v0 < g.TP; v0 += 8) {
+                            blk += 8;
+                            if (blk >= g.RING) blk -= g.RING;
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) wc[8 + m] = hc[(size_t)(blk + m) * g.HB_SLOT];
+                            const float4 ta = *reinterpret_cast<const float4 *>(taps + v0);
+                            const float4 tb = *reinterpret_cast<const float4 *>(taps + v0 + 4);
+                            const float tv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
+#pragma unroll
+                            for (int vv = 0; vv < 8; ++vv)
+#pragma unroll
+                                for (int m = 0; m < 8; ++m) vc[m] = fmaf(tv[vv], wc[m + vv], vc[m]);
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) wc[m] = wc[m + 8];
+                        }
+                        int crow = (o0 + r) % g.RING_CS;
+                        float *acc = ACC + ((size_t)p * BY + o0) * kBX + x;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            const float2 cs = CS[crow * kBX + x];
+                            acc[m * kBX] += (gi == 0 ? cs.x : cs.y) * vc[m];
+                            if (++crow == g.RING_CS) crow = 0;
+                        }
                     }
                 }
             }
@@ -215,7 +268,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // and CS slots that C does not read (RING_CS has one spare chunk);
             // the barrier after that A orders this C before the next B.
         }
-        __syncthreads();  // term boundary: CS/HB slots are reused from row 0
+        __syncthreads();  // pass / term boundary: CS/HB slots are reused from row 0
+      }
     }
     // ---------------- divide and store -----------------------------------------
     for (int idx = tid; idx < BY * kBX; idx += kThreads) {
@@ -230,35 +284,43 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-template <int D>
-int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s) {
-    int dev = 0, max_smem = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // tallest tile (multiple of kRC, at most 128 rows) whose buffers fit
+// Tallest tile (multiple of kRC, at most 128 rows) whose buffers fit; 0 if none.
+template <int D, int G>
+int fit_rows(int r, int H, int max_smem) {
     int BY = 128;
-    Geom g = make_geom<D>(p.r, BY);
-    while (BY > kRC && g.smem_floats * sizeof(float) > (size_t)max_smem) {
-        BY -= kRC;
-        g = make_geom<D>(p.r, BY);
-    }
-    if (BY > H) {  // short image: no taller than needed
-        int by = kRC * cdiv(H, kRC);
-        if (by < BY) {
-            BY = by;
-            g = make_geom<D>(p.r, BY);
-        }
-    }
+    while (BY >= kRC && make_geom<D, G>(r, BY).smem_floats * sizeof(float) > (size_t)max_smem) BY -= kRC;
+    if (BY < kRC) return 0;
+    const int by = kRC * cdiv(H, kRC);  // short image: no taller than needed
+    return by < BY ? by : BY;
+}
+
+template <int D, int G>
+int launch_dg(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int BY, cudaStream_t s) {
+    const Geom g = make_geom<D, G>(p.r, BY);
     const size_t bytes = g.smem_floats * sizeof(float);
-    if (bytes > (size_t)max_smem) return BF_ERR_UNSUPPORTED;
-    cudaError_t e = cudaFuncSetAttribute(mcsf_fp32_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(mcsf_fp32_kernel<D, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return BF_ERR_CUDA;
     }
     dim3 grid(cdiv(W, kBX), cdiv(H, BY));
-    mcsf_fp32_kernel<D><<<grid, kThreads, bytes, s>>>(in, out, H, W, pitch, p.nu_hi, p.nu_lo, p.K, p.taps, g);
+    mcsf_fp32_kernel<D, G><<<grid, kThreads, bytes, s>>>(in, out, H, W, pitch, p.nu_hi, p.nu_lo, p.K, p.taps, g);
     return cuda_err(cudaGetLastError());
+}
+
+// One pass per term when a tile of at least 32 rows fits, else two passes
+// (channel groups), else BF_ERR_UNSUPPORTED.
+template <int D>
+int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s) {
+    int dev = 0, max_smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int by1 = fit_rows<D, 1>(p.r, H, max_smem);
+    if (by1 >= 32 || (by1 > 0 && by1 >= kRC * cdiv(H, kRC))) return launch_dg<D, 1>(p, in, out, H, W, pitch, by1, s);
+    const int by2 = fit_rows<D, 2>(p.r, H, max_smem);
+    if (by2 > 0) return launch_dg<D, 2>(p, in, out, H, W, pitch, by2, s);
+    if (by1 > 0) return launch_dg<D, 1>(p, in, out, H, W, pitch, by1, s);
+    return BF_ERR_UNSUPPORTED;
 }
 
 }  // namespace

@@ -1,0 +1,212 @@
+"""Request loop for the filter: continuous batching under a device-memory
+budget.
+
+Requests (one image each, with its own d, sigma_s, C, N, K, seed) arrive at any
+time.  The server
+  * keeps plans (sampled, whitened frequency lists) resident on the device in
+    an LRU cache keyed by (d, C, sigma_s, N, K, seed, whitening);
+  * admits queued requests in arrival order while the device memory they need
+    (their output buffer; inputs are the caller's) fits in the budget, and
+    rejects a request larger than the whole budget;
+  * launches whatever has been admitted as one bf_filter_batch call on the
+    next free stream as soon as one is free, so requests that arrive while
+    others are on the GPU join the next batch and their work overlaps the
+    batches already running (continuous batching);
+  * completes requests as their batch's event fires, frees their budget and
+    records per-request latency (arrival to completion).
+Every filtering step runs in libbf's kernels; this module only schedules.
+"""
+from __future__ import annotations
+
+import collections
+import math
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import bf
+
+__all__ = ["Request", "Server", "summarize"]
+
+
+@dataclass
+class Request:
+    """One image to filter.  `x` is a CUDA float32 tensor (d, H, W) with unit
+    column stride and a row stride that is a multiple of 4 (see
+    bf.pitched_empty); the result goes to `out` (allocated on admission)."""
+    x: object
+    C: np.ndarray
+    sigma_s: float
+    K: int
+    N: int = 10
+    seed: int = 0
+    whiten: int = bf.BF_WHITEN_CHOLESKY
+    t_arrival: float = 0.0
+    rid: int = 0
+    out: object = None
+    t_admit: float = math.nan
+    t_done: float = math.nan
+    status: int = 1  # 1 pending, 0 done, < 0 BF_ERR_*
+    _bytes: int = 0
+    done_evt: threading.Event = field(default_factory=threading.Event)
+
+    @property
+    def latency(self) -> float:
+        return self.t_done - self.t_arrival
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 40 << 30, streams: int = 2, max_batch: int = 64,
+                 variant: int = bf.BF_FP16TC, plan_cache: int = 256, device: int = 0):
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.budget = int(budget_bytes)
+        self.used = 0
+        self.variant = variant
+        self.max_batch = max_batch
+        self.streams = [torch.cuda.Stream(device=self.dev) for _ in range(streams)]
+        self.busy = [None] * streams            # (event, requests) of the batch in flight per stream
+        self.queue: collections.deque[Request] = collections.deque()
+        self.plans: collections.OrderedDict = collections.OrderedDict()
+        self.plan_cache = plan_cache
+        self.lock = threading.Lock()
+        self.cv = threading.Condition(self.lock)
+        self.closed = False
+        self.completed: list[Request] = []
+        self.rejected: list[Request] = []
+        self.batches = 0
+        self._thread = None
+
+    # -- plans -------------------------------------------------------------------
+    def plan(self, d: int, C, sigma_s: float, N: int, K: int, seed: int, whiten: int = 0) -> bf.Plan:
+        key = (d, np.ascontiguousarray(C, np.float64).tobytes(), float(sigma_s), N, K, seed, whiten)
+        p = self.plans.get(key)
+        if p is None:
+            p = bf.bf_plan(d, C, sigma_s, N, K, seed, whiten)
+            self.plans[key] = p
+            while len(self.plans) > self.plan_cache:
+                self.plans.popitem(last=False)  # its handle is released when unreferenced
+        else:
+            self.plans.move_to_end(key)
+        return p
+
+    # -- client side -------------------------------------------------------------------
+    def submit(self, req: Request) -> Request:
+        if not req.t_arrival:
+            req.t_arrival = time.perf_counter()
+        d, H, W = req.x.shape
+        req._bytes = d * H * req.x.stride(1) * 4
+        with self.cv:
+            if req._bytes > self.budget:
+                req.status = bf.BF_ERR_BUDGET
+                req.t_done = time.perf_counter()
+                self.rejected.append(req)
+                req.done_evt.set()
+                return req
+            self.queue.append(req)
+            self.cv.notify()
+        return req
+
+    def start(self):
+        self._thread = threading.Thread(target=self._loop, name="bf-serve", daemon=True)
+        self._thread.start()
+        return self
+
+    def close(self, wait: bool = True):
+        with self.cv:
+            self.closed = True
+            self.cv.notify()
+        if wait and self._thread:
+            self._thread.join()
+
+    # -- scheduler -----------------------------------------------------------------
+    def _finish(self, i: int):
+        evt, reqs = self.busy[i]
+        evt.synchronize()
+        now = time.perf_counter()
+        with self.cv:
+            for r in reqs:
+                r.t_done = now
+                if r.status == 1:
+                    r.status = 0
+                self.used -= r._bytes
+                self.completed.append(r)
+                r.done_evt.set()
+            self.busy[i] = None
+
+    def _admit(self) -> list[Request]:
+        """Admit queued requests in arrival order while the budget allows."""
+        batch = []
+        with self.cv:
+            while self.queue and len(batch) < self.max_batch and self.used + self.queue[0]._bytes <= self.budget:
+                r = self.queue.popleft()
+                self.used += r._bytes
+                batch.append(r)
+        return batch
+
+    def _launch(self, i: int, batch: list[Request]):
+        torch = self.torch
+        s = self.streams[i]
+        now = time.perf_counter()
+        tc, fp = [], []
+        with torch.cuda.stream(s):
+            for r in batch:
+                r.t_admit = now
+                d, H, W = r.x.shape
+                r.out = torch.empty_strided(r.x.shape, r.x.stride(), dtype=torch.float32, device=self.dev)
+                p = self.plan(d, r.C, r.sigma_s, r.N, r.K, r.seed, r.whiten)
+                item = (p, r.x.data_ptr(), r.out.data_ptr(), H, W, r.x.stride(1))
+                (tc if (self.variant != bf.BF_FP32 and d == 3) else fp).append(item)
+            try:
+                if tc:
+                    bf.bf_filter_batch(tc, self.variant, s.cuda_stream)
+                if fp:
+                    bf.bf_filter_batch(fp, bf.BF_FP32, s.cuda_stream)
+            except bf.BFError as e:
+                for r in batch:
+                    r.status = e.code
+            evt = torch.cuda.Event()
+            evt.record(s)
+        self.busy[i] = (evt, batch)
+        self.batches += 1
+
+    def _loop(self):
+        torch = self.torch
+        torch.cuda.set_device(self.dev)
+        while True:
+            progressed = False
+            for i, b in enumerate(self.busy):
+                if b is not None and b[0].query():
+                    self._finish(i)
+                    progressed = True
+            free = [i for i, b in enumerate(self.busy) if b is None]
+            if free:
+                batch = self._admit()
+                if batch:
+                    self._launch(free[0], batch)
+                    progressed = True
+            with self.cv:
+                idle = not self.queue and all(b is None for b in self.busy)
+                if self.closed and idle:
+                    return
+                if not progressed:
+                    if not self.queue and all(b is None for b in self.busy):
+                        self.cv.wait(timeout=0.01)
+            if not progressed:
+                time.sleep(50e-6)
+
+
+def summarize(reqs: list[Request], t0: float, t1: float) -> dict:
+    """Images/s, Mpixel/s and latency percentiles of completed requests."""
+    done = [r for r in reqs if r.status == 0]
+    lat = np.array([r.latency for r in done]) if done else np.array([math.nan])
+    px = sum(r.x.shape[1] * r.x.shape[2] for r in done)
+    span = max(t1 - t0, 1e-9)
+    return {"completed": len(done), "rejected": sum(1 for r in reqs if r.status == bf.BF_ERR_BUDGET),
+            "failed": sum(1 for r in reqs if r.status < 0 and r.status != bf.BF_ERR_BUDGET),
+            "images_per_s": len(done) / span, "mpixel_per_s": px / span / 1e6,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "span_s": span}

@@ -119,9 +119,17 @@ def test_fp32_small_config_full_image(bf):
     (3, 9, 11, 5.0, 10, 8, 7),       # image smaller than the window
     (3, 64, 64, 8.0, 10, 1, 8),      # K = 1, widest configured window
     (3, 20, 33, 0.2, 10, 4, 9),      # r = 0: the window is the pixel alone
+    (6, 60, 50, 2.0, 10, 8, 14),     # 6 channels, one pass per term
+    (6, 50, 70, 8.0, 10, 24, 12),    # 6 channels, r = 24: cos and sin groups in two passes
+    (8, 40, 45, 10.5, 10, 24, 13),   # 8 channels, r = 31: two passes
 ])
 def test_fp32_ragged_and_edge_shapes(bf, d, H, W, s, N, K, seed):
-    C = synth.spd_cond(d, seed=300 + seed) if d > 1 else np.array([[35.0 ** 2]])
+    if d == 1:
+        C = np.array([[35.0 ** 2]])
+    elif d >= 6:  # wider range kernel: in 6-8 dimensions a sigma_r of 20-40 leaves Z near zero
+        C = synth.spd_cond(d, seed=300 + seed, lam_min_range=(50.0 ** 2, 70.0 ** 2))
+    else:
+        C = synth.spd_cond(d, seed=300 + seed)
     f = synth.voronoi_image(H, W, d, 6, 10.0, seed=seed)
     plan = bf.bf_plan(d, C, s, N, K, 99 + seed)
     got = _run(bf, plan, f, bf.BF_FP32)

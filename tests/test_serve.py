@@ -1,0 +1,94 @@
+"""The request loop: continuous batching gives every request the same result
+it gets alone, admission respects the memory budget, and a request larger than
+the whole budget is rejected with BF_ERR_BUDGET."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_1605_02164_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+
+@pytest.fixture(scope="module")
+def bf():
+    from paper_1605_02164_gb300 import bf as _bf
+    from paper_1605_02164_gb300 import build
+    build.build()
+    _bf.lib()
+    return _bf
+
+
+def _requests(bf, n, seed):
+    from paper_1605_02164_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for i in range(n):
+        H, W = int(rng.integers(40, 300)), int(rng.integers(40, 300))
+        d = 3 if i % 4 else 1  # grayscale requests go through the FP32 kernel in the same batch
+        s = float(rng.uniform(1.0, 6.0))
+        sr = float(rng.uniform(20, 60))
+        f = synth.voronoi_image(H, W, d, 6, 10.0, seed=seed * 100 + i)
+        reqs.append(Request(bf.to_pitched(f), np.diag([sr * sr] * d), s, int(rng.choice([16, 32])), 10,
+                            seed=seed + i, rid=i))
+    return reqs
+
+
+def _alone(bf, r, variant):
+    p = bf.bf_plan(r.x.shape[0], r.C, r.sigma_s, r.N, r.K, r.seed)
+    v = variant if r.x.shape[0] == 3 else bf.BF_FP32
+    y = bf.filter_tensor(p, r.x, v)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+@pytest.mark.parametrize("variant", ["fp16tc", "fp32"])
+def test_results_same_alone_and_in_the_mix(bf, variant):
+    from paper_1605_02164_gb300.serve import Server
+    v = bf.VARIANTS[variant]
+    reqs = _requests(bf, 16, seed=7)
+    srv = Server(budget_bytes=64 << 20, streams=2, max_batch=5, variant=v).start()
+
+    def client(rs):
+        for r in rs:
+            srv.submit(r)
+            time.sleep(0.002)  # arrivals interleave with batches already on the GPU
+
+    ts = [threading.Thread(target=client, args=(reqs[k::2],)) for k in range(2)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for r in reqs:
+        assert r.done_evt.wait(120)
+    srv.close()
+    assert srv.batches >= 2
+    assert all(r.status == 0 for r in reqs)
+    for r in reqs:
+        assert np.array_equal(r.out.cpu().numpy(), _alone(bf, r, v)), r.rid
+    assert bf.bf_last_status(0) == bf.BF_OK
+
+
+def test_budget_admission_and_rejection(bf):
+    from paper_1605_02164_gb300.serve import Request, Server, summarize
+    reqs = _requests(bf, 6, seed=3)
+    one = max(r.x.shape[0] * r.x.shape[1] * r.x.stride(1) * 4 for r in reqs)
+    srv = Server(budget_bytes=one, streams=2, max_batch=8).start()  # at most one large request in flight
+    big = Request(bf.to_pitched(synth.voronoi_image(400, 400, 3, 4, 10.0, seed=1)), np.diag([900.0] * 3),
+                  2.0, 8, 10, seed=1, rid=99)
+    t0 = time.perf_counter()
+    for r in reqs:
+        srv.submit(r)
+    if big.x.shape[0] * big.x.shape[1] * big.x.stride(1) * 4 > one:
+        srv.submit(big)
+        assert big.status == bf.BF_ERR_BUDGET
+    for r in reqs:
+        assert r.done_evt.wait(120)
+    srv.close()
+    s = summarize(reqs, t0, time.perf_counter())
+    assert s["completed"] == len(reqs) and s["failed"] == 0
+    assert srv.used == 0
