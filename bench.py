@@ -313,6 +313,169 @@ def run_ours(args):
     return 0
 
 
+def _split_items(bf, items_and_d, variant):
+    """Tensor-core launches take the d = 3 images; other d run on the FP32 kernel."""
+    tc = [it for it, d in items_and_d if d == 3 and variant != bf.BF_FP32]
+    fp = [it for it, d in items_and_d if not (d == 3 and variant != bf.BF_FP32)]
+    return tc, fp
+
+
+def run_batch(args):
+    """Uneven batch: 64 images, sizes U[256, 2048] x U[256, 1536], d in {3, 6},
+    sigma_s ~ U[2, 10], C with condition number <= 10, K in {32, 64, 128}.
+    One persistent launch (d = 3 on the tensor cores, d = 6 on the FP32
+    kernel) against one launch per image, and the plain FP32 path."""
+    import torch
+    from paper_1605_02164_gb300 import bf
+    from paper_1605_02164_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    variant = bf.VARIANTS[args.variant]
+    ws = synth.batch_items(args.batch_n, seed=4000)
+    items, plans, bufs, px = [], [], [], 0
+    for w in ws:
+        f = synth.voronoi_image(w.H, w.W, w.d, 16, w.noise, seed=w.seed)
+        p = bf.bf_plan(w.d, w.C, w.sigma_s, w.N, w.K, w.seed)
+        x = bf.to_pitched(f)
+        y = bf.pitched_empty(w.d, w.H, w.W)
+        plans.append(p)
+        bufs.append((x, y))
+        items.append(((p, x.data_ptr(), y.data_ptr(), w.H, w.W, x.stride(1)), w.d))
+        px += w.H * w.W
+    sp = torch.cuda.current_stream().cuda_stream
+    tc, fp = _split_items(bf, items, variant)
+
+    def batched():
+        if tc:
+            bf.bf_filter_batch(tc, variant, sp)
+        if fp:
+            bf.bf_filter_batch(fp, bf.BF_FP32, sp)
+
+    def per_image(v):
+        for it, d in items:
+            bf.bf_filter(*it, v if (d == 3 or v == bf.BF_FP32) else bf.BF_FP32, sp)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms_batch = timed(batched, args.steps)
+    ms_single = timed(lambda: per_image(variant), max(1, args.steps // 2))
+    ms_fp32 = timed(lambda: per_image(bf.BF_FP32), 1)
+    line = {"metric": "Mpixel/s (uneven batch)", "value": px / ms_batch / 1e3, "unit": "Mpixel/s", "n_gpus": 1,
+            "steps": args.steps, "ms_per_step": ms_batch, "higher_is_better": True, "dtype": args.variant,
+            "data": "synthetic",
+            "config": {"workload": f"batch{len(ws)}_sizes256-2048x256-1536_d3or6_s2-10_K32-128",
+                       "images": len(ws), "mpixel": px / 1e6, "d3_images": len(tc), "d6_images": len(fp)},
+            "per_image_launches_mpx": px / ms_single / 1e3, "plain_fp32_mpx": px / ms_fp32 / 1e3,
+            "images_per_s": len(ws) / ms_batch * 1e3}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args):
+    """Open-loop Poisson trace (2000 requests/s) of square RGB images with area
+    log-uniform in [512^2, 4096^2], sigma_s ~ U[2, 10], C = sigma_r^2 I with
+    sigma_r ~ U[20, 60], K = 64, through the request loop (continuous batching
+    under a 40 GB output budget) and through plain per-image FP32 launches."""
+    import torch
+    from paper_1605_02164_gb300 import bf
+    from paper_1605_02164_gb300 import build as B
+    from paper_1605_02164_gb300.serve import Request, Server, summarize
+    B.build()
+    torch.cuda.set_device(0)
+    trace = synth.serving_trace(args.serve_seconds, 2000.0, seed=5000)
+    big = torch.from_numpy(synth.voronoi_image(4096, 4096, 3, 64, 10.0, seed=5001)).cuda()
+    side = torch.cuda.Stream()
+
+    def make_input(w, i):
+        y0 = (i * 977) % (4096 - w.H + 1)
+        x0 = (i * 613) % (4096 - w.W + 1)
+        with torch.cuda.stream(side):
+            x = bf.pitched_empty(3, w.H, w.W)
+            x.copy_(big[:, y0:y0 + w.H, x0:x0 + w.W])
+        side.synchronize()
+        return x
+
+    def replay(submit):
+        reqs = []
+        t0 = time.perf_counter()
+        for i, (ta, w) in enumerate(trace):
+            x = make_input(w, i)
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            r = Request(x, w.C, w.sigma_s, w.K, w.N, seed=w.seed, rid=i, t_arrival=t0 + ta)
+            submit(r)
+            reqs.append(r)
+        return t0, reqs
+
+    variant = bf.VARIANTS[args.variant]
+    srv = Server(budget_bytes=40 << 30, streams=3, max_batch=64, variant=variant).start()
+    t0, reqs = replay(srv.submit)
+    for r in reqs:
+        r.done_evt.wait()
+    t1 = time.perf_counter()
+    srv.close()
+    served = summarize(reqs, t0, t1)
+    served["batches"] = srv.batches
+    for r in reqs:
+        r.out = None
+
+    # plain per-image FP32 launches on the same trace, one stream, in arrival order
+    plans = {}
+    done = []
+    q = []
+    lock = threading.Lock()
+    stop = threading.Event()
+
+    def worker():
+        s = torch.cuda.Stream()
+        while not (stop.is_set() and not q):
+            with lock:
+                r = q.pop(0) if q else None
+            if r is None:
+                time.sleep(1e-4)
+                continue
+            key = (r.sigma_s, r.C.tobytes(), r.K, r.seed)
+            p = plans.get(key) or plans.setdefault(key, bf.bf_plan(3, r.C, r.sigma_s, r.N, r.K, r.seed))
+            with torch.cuda.stream(s):
+                r.out = bf.filter_tensor(p, r.x, bf.BF_FP32, stream=s)
+            s.synchronize()
+            r.t_done = time.perf_counter()
+            r.status = 0
+            r.out = None
+            done.append(r)
+
+    th = threading.Thread(target=worker, daemon=True)
+    th.start()
+
+    def submit_plain(r):
+        with lock:
+            q.append(r)
+
+    t0b, reqs_b = replay(submit_plain)
+    stop.set()
+    th.join()
+    plain = summarize(reqs_b, t0b, time.perf_counter())
+    line = {"metric": "images/s (serving trace)", "value": served["images_per_s"], "unit": "images/s",
+            "n_gpus": 1, "higher_is_better": True, "dtype": args.variant, "data": "synthetic",
+            "config": {"workload": "serve_poisson2000_rgb512-4096_s2-10_sr20-60_K64",
+                       "arrival_seconds": args.serve_seconds, "requests": len(trace), "budget_gb": 40,
+                       "streams": 3, "max_batch": 64},
+            "served": served, "plain_fp32_per_image": plain,
+            "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -320,7 +483,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="fp16tc", choices=["fp32", "fp16tc", "bf16tc"])
-    ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--batch-n", type=int, default=64)
+    ap.add_argument("--serve-seconds", type=float, default=0.25)
     ap.add_argument("--seed", type=int, default=3000)
     ap.add_argument("--cpu-crop", type=int, default=1536)
     ap.add_argument("--ref-crop", type=int, default=512)
@@ -331,6 +496,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 
