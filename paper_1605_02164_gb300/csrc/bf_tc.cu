@@ -37,7 +37,7 @@
 namespace bf {
 namespace {
 
-constexpr int kT = 256;  // 8 warps: channels, transpose, combine; lane 0 of warps 0 and 4-7 also issue MMAs
+constexpr int kT = 512;  // 16 warps: channels, transpose, combine; lane 0 of warps 0 and 4-7 also issue MMAs
 constexpr int kBX = 64;        // output columns per tile
 constexpr int kNC = 8;         // 16-row chunks per region (128 rows)
 constexpr int kNOC = 5;        // output chunks (of 16 rows) per tile at most
@@ -127,6 +127,21 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void tmem_ld4(uint32_t a, float *v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st4(uint32_t a, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(__float_as_uint(v[0])),
+                 "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3]))
+                 : "memory");
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t a, float *v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -148,14 +163,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t a, float *v) {
 }
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_st8(uint32_t a, const float *v) {
-    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(a),
-                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7]))
-                 : "memory");
-}
 
 template <bool BF16>
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
@@ -221,9 +228,11 @@ __global__ void __launch_bounds__(kT, 1)
     float2 *ring = reinterpret_cast<float2 *>(sm + lay.offC);  // [ringC][64] centre (cos, sin), see ring_idx
     int *counter = ctrl;
 
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1;
+    // Warp w works on TMEM lane quarter q = w & 3 (the lanes it may access),
+    // x half h, and half e of the 8-pixel groups / of the 16 rows of a block.
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1, e = w >> 3;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const int row = l & 15, xg = 2 * w + (l >> 4);
+    const int row = l & 15, xg = 2 * (w & 7) + (l >> 4), px0 = 4 * e;
 
     // ---- once per CTA: tensor memory, barriers ------------------------------------
     if (w == 0) {
@@ -286,41 +295,42 @@ __global__ void __launch_bounds__(kT, 1)
         }
 
         // ---- region f -> tensor memory; in-image masks -------------------------------
-        // Thread (w, l) owns region row 16c + row, columns 8 xg .. 8 xg + 7 of
-        // every chunk c, stored in its TMEM lane at columns (2c + h)*24 + ch*8 + j.
-        uint64_t vmask = 0;  // bit 8c + j: pixel inside the image
-        uint32_t cmask = 0;  // bit j: column is a centre (output) column
+        // The 8-pixel group (region row 16c + row, columns 8 xg .. 8 xg + 7) of
+        // every chunk c lives in TMEM lane 32q + l at columns (2c + h)*24 +
+        // ch*8 + j; this thread owns its pixels j = px0 .. px0 + 3.
+        uint32_t vmask = 0;  // bit 4c + jj: pixel px0 + jj inside the image
+        uint32_t cmask = 0;  // bit jj: column is a centre (output) column
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int cx = 8 * xg + j - r;
-            if (cx >= 0 && cx < kBX) cmask |= 1u << j;
+        for (int jj = 0; jj < 4; ++jj) {
+            const int cx = 8 * xg + px0 + jj - r;
+            if (cx >= 0 && cx < kBX) cmask |= 1u << jj;
         }
         for (int c = 0; c < kNC; ++c) {
             const int gy = ry0 + 16 * c + row;
             const bool rowv = gy >= 0 && gy < H;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int gx = rx0 + 8 * xg + j;
-                if (rowv && gx >= 0 && gx < W) vmask |= 1ull << (8 * c + j);
+            for (int jj = 0; jj < 4; ++jj) {
+                const int gx = rx0 + 8 * xg + px0 + jj;
+                if (rowv && gx >= 0 && gx < W) vmask |= 1u << (4 * c + jj);
             }
 #pragma unroll
             for (int ch = 0; ch < 3; ++ch) {
-                float v[8];
+                float v[4];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    v[j] = ((vmask >> (8 * c + j)) & 1)
-                               ? __ldg(in + ch * plane + (size_t)(ry0 + 16 * c + row) * pitch + (rx0 + 8 * xg + j))
-                               : 0.f;
-                tmem_st8(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8, v);
+                for (int jj = 0; jj < 4; ++jj)
+                    v[jj] = ((vmask >> (4 * c + jj)) & 1)
+                                ? __ldg(in + ch * plane + (size_t)(ry0 + 16 * c + row) * pitch + (rx0 + 8 * xg + px0 + jj))
+                                : 0.f;
+                tmem_st4(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8 + px0, v);
             }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 
-        float acc[NOC][16];
+        float acc[NOC][8];  // rows 16 o + 8 e + j of this thread's (channel, column)
 #pragma unroll
         for (int o = 0; o < NOC; ++o)
 #pragma unroll
-            for (int j = 0; j < 16; ++j) acc[o][j] = 0.f;
+            for (int j = 0; j < 8; ++j) acc[o][j] = 0.f;
 
         const int NCr = g.nc;  // 16-row chunks per term: ceil((BY + 2r) / 16) <= 8
         const int S = K * NCr;
@@ -330,32 +340,32 @@ __global__ void __launch_bounds__(kT, 1)
         auto stage_A = [&](int s) {
             const int k = s / NCr, c = s - k * NCr;
             const float n0 = __ldg(nu_hi + 3 * k), n1 = __ldg(nu_hi + 3 * k + 1), n2 = __ldg(nu_hi + 3 * k + 2);
-            float f0[8], f1[8], f2[8];
-            const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24;
-            tmem_ld8(fa, f0);
-            tmem_ld8(fa + 8, f1);
-            tmem_ld8(fa + 16, f2);
+            float f0[4], f1[4], f2[4];
+            const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24 + px0;
+            tmem_ld4(fa, f0);
+            tmem_ld4(fa + 8, f1);
+            tmem_ld4(fa + 16, f2);
             tmem_wait_ld();
-            const uint32_t vm = (uint32_t)(vmask >> (8 * c)) & 0xFFu;
+            const uint32_t vm = (vmask >> (4 * c)) & 0xFu;
             const int ry = 16 * c + row;
             const bool centre_row = ry >= r && ry < r + BY && cmask;
-            uint32_t o[8][4];
-            float csv[8], snv[8];
-    #pragma unroll
-            for (int p = 0; p < 4; ++p) {
+            uint32_t o[8][2];
+            float csv[4], snv[4];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
                 float cv[2], sv[2];
-    #pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int j = 2 * p + e;
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int j = 2 * p + u;
                     const float t = fmaf(n0, f0[j], fmaf(n1, f1[j], n2 * f2[j]));
                     const float fr = t - rintf(t);
                     float s_, c_;
                     __sincosf(6.28318530717958647692f * fr, &s_, &c_);
                     const bool v = (vm >> j) & 1u;
-                    cv[e] = v ? c_ : 0.f;
-                    sv[e] = v ? s_ : 0.f;
-                    csv[j] = cv[e];
-                    snv[j] = sv[e];
+                    cv[u] = v ? c_ : 0.f;
+                    sv[u] = v ? s_ : 0.f;
+                    csv[j] = cv[u];
+                    snv[j] = sv[u];
                 }
                 const typename P2::T hc = P2::make(cv[0], cv[1]);
                 const typename P2::T hs = P2::make(sv[0], sv[1]);
@@ -382,31 +392,32 @@ __global__ void __launch_bounds__(kT, 1)
                     o[6][p] = bits(__hmul2(hs, g2));
                 }
             }
-            if (centre_row) {  // centre cos/sin for the combine, slot = flat region row mod 128
+            if (centre_row) {  // centre cos/sin for the combine, slot = flat region row mod ringC
                 const int slot = (16 * s + row) % g.ringC;
-    #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if ((cmask >> j) & 1u) ring[ring_idx(slot, 8 * xg + j - r)] = make_float2(csv[j], snv[j]);
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj)
+                    if ((cmask >> jj) & 1u) ring[ring_idx(slot, 8 * xg + px0 + jj - r)] = make_float2(csv[jj], snv[jj]);
             }
-            uint8_t *dst = A1 + (s & 1) * 32768 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048;
-    #pragma unroll
+            // 4 pixels of one channel = the e-th half of a 16-byte core-matrix row
+            uint8_t *dst = A1 + (s & 1) * 32768 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048 + 8 * e;
+#pragma unroll
             for (int ch = 0; ch < 8; ++ch)
-                *reinterpret_cast<uint4 *>(dst + ch * 4096) = make_uint4(o[ch][0], o[ch][1], o[ch][2], o[ch][3]);
+                *reinterpret_cast<uint2 *>(dst + ch * 4096) = make_uint2(o[ch][0], o[ch][1]);
         };
 
         // C: combine output chunk oc (its window starts at flat step s_first)
         auto stage_C = [&](int oc, int s_first) {
-            float vc[16], vs[16];
-            tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h), vc);
-            tmem_ld16(tmem + lane_base + kColD2 + 16 * (2 * h + 1), vs);
+            float vc[8], vs[8];  // output rows 16 oc + 8 e + j of the cos / sin M-tile
+            tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h) + 8 * e, vc);
+            tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h + 1) + 8 * e, vs);
             tmem_wait_ld();
             const int x = 32 * h + l;
-            int slot = (16 * s_first + r) % g.ringC;  // flat region row of output row 16 oc
-    #pragma unroll
+            int slot = (16 * s_first + r + 8 * e) % g.ringC;  // flat region row of output row 16 oc + 8 e
+#pragma unroll
             for (int o = 0; o < NOC; ++o) {
                 if (o == oc) {
-    #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
                         const float2 cs = ring[ring_idx(slot, x)];
                         if (++slot == g.ringC) slot = 0;
                         acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
@@ -417,16 +428,15 @@ __global__ void __launch_bounds__(kT, 1)
 
         // X: D1 of flat step s -> A2 ring
         auto stage_X = [&](int s) {
-            float v[32];
-            const uint32_t da = tmem + lane_base + kColD1 + 32 * h;
-            tmem_ld16(da, v);
-            tmem_ld16(da + 16, v + 16);
+            float v[16];  // output columns 32 h + 16 e .. + 15 of this (channel, row)
+            tmem_ld16(tmem + lane_base + kColD1 + 32 * h + 16 * e, v);
             tmem_wait_ld();
             const int ch = 2 * q + (l >> 4), gsel = ch >> 2, p = ch & 3;
             const int kr = (16 * s + row) % g.Kw;
-            uint8_t *base = A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512;
-    #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+            uint8_t *base =
+                A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512 + 2 * e * 128;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
                 const uint4 pk = make_uint4(bits(P2::make(v[8 * i], v[8 * i + 1])), bits(P2::make(v[8 * i + 2], v[8 * i + 3])),
                                             bits(P2::make(v[8 * i + 4], v[8 * i + 5])),
                                             bits(P2::make(v[8 * i + 6], v[8 * i + 7])));
@@ -438,14 +448,14 @@ __global__ void __launch_bounds__(kT, 1)
         // added to the 14-bit start-address field (address >> 4).
         auto issue_M1 = [&](int s) {
             const uint64_t a = dA1 + (uint64_t)((s & 1) * (32768 >> 4));
-    #pragma unroll
+#pragma unroll
             for (int ks = 0; ks < 8; ++ks)
                 if (ks < g.ks1) mma_f16(tmem + kColD1, a + 16 * ks, dB1 + 128 * ks, id1, ks > 0);
             mma_commit(&mbar[0]);
         };
         auto issue_M2 = [&](int s_first, int t) {  // M-tile t of the vertical pass
             const int kgb = (2 * s_first) % kgring;
-    #pragma unroll
+#pragma unroll
             for (int ks = 0; ks < 5; ++ks)
                 if (ks < g.ksteps) {
                     int kg0 = kgb + 2 * ks;
@@ -489,7 +499,7 @@ __global__ void __launch_bounds__(kT, 1)
             if (timed_out) abort_s = 1;
             __syncthreads();
             if (abort_s) goto cleanup;
-            if (l == 0 && (w == 0 || (w >= 4 && do_m2))) {
+            if (l == 0 && (w == 0 || (w >= 4 && w < 8 && do_m2))) {
                 fence_after();
                 if (w == 0) {
                     if (s + 1 < S) issue_M1(s + 1);
@@ -522,8 +532,8 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
                 for (int o = 0; o < NOC; ++o)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (16 * o + j < BY) zbuf[(16 * o + j) * kBX + x] = acc[o][j];
+                    for (int j = 0; j < 8; ++j)
+                        if (16 * o + 8 * e + j < BY) zbuf[(16 * o + 8 * e + j) * kBX + x] = acc[o][j];
             }
             __syncthreads();
             const int gx = tx0 + x;
@@ -531,8 +541,8 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
                 for (int o = 0; o < NOC; ++o)
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int y = 16 * o + j, gy = ty0 + y;
+                    for (int j = 0; j < 8; ++j) {
+                        const int y = 16 * o + 8 * e + j, gy = ty0 + y;
                         if (y < BY && gy < H)
                             out[q * plane + (size_t)gy * pitch + gx] = acc[o][j] / zbuf[y * kBX + x];
                     }
@@ -544,7 +554,7 @@ __global__ void __launch_bounds__(kT, 1)
     }
 
 cleanup:
-    if (abort_s && l == 0 && (w == 0 || w >= 4)) {
+    if (abort_s && l == 0 && (w == 0 || (w >= 4 && w < 8))) {
         if (w == 0) atomicCAS(status, 0, BF_ERR_TIMEOUT);
         // drain: bounded wait for every MMA this thread issued (fresh barrier phase)
         mma_commit(&mbar[0]);
