@@ -46,12 +46,13 @@ constexpr uint32_t kColD1 = 384;
 constexpr uint32_t kColD2 = 448;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSpinLimit = 1 << 22;
-// Centre ring: float2 (cos, sin) per output column, rows = flat region rows mod
-// ringC = 16 (lag + 3) (a multiple of 16, so slot & 15 is the row in its chunk);
-// column c of slot row t is stored at t * kBX + (c ^ (t & 15)) so that the 16
-// rows a warp writes at one column and the 32 columns it reads in one row both
-// fall on distinct banks.
-__device__ __forceinline__ int ring_idx(int slot, int col) { return slot * kBX + (col ^ (slot & 15)); }
+// Centre ring: float2 (cos, sin) per output column; ring row t holds flat output
+// row t mod ringC, ringC = 16 (lag + 3) (flat output row = flat region row - r).
+// Column c of ring row t is stored at t * kBX + (c ^ ring_xor(t)): whatever r,
+// the 16 rows a half-warp writes (rows 8-15 four pixels to the side of rows 0-7,
+// see px0) and the 32 columns a warp reads in one row fall on distinct banks.
+// A combine reads 8 rows starting at a multiple of 8, so its XORs are constants.
+__host__ __device__ constexpr int ring_xor(int t) { return (t & 3) | ((t & 4) << 1); }
 
 // One image of a launch (the single-image call is a batch of one).  The table
 // lives in device memory; tiles of all images form one work queue.
@@ -225,14 +226,18 @@ __global__ void __launch_bounds__(kT, 1)
     uint8_t *A2 = sm + lay.offA2;   // [kg Kw/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
     uint8_t *B1 = sm + lay.offB1;   // [kg Kw1/8][ng 8][8 n][16 B]  K-major band, horizontal pass (N = 64)
     uint8_t *B2 = sm + lay.offB;    // [kg Kw/8][ng 2][8 n][16 B]   K-major band, vertical pass (N = 16)
-    float2 *ring = reinterpret_cast<float2 *>(sm + lay.offC);  // [ringC][64] centre (cos, sin), see ring_idx
+    float2 *ring = reinterpret_cast<float2 *>(sm + lay.offC);  // [ringC][64] centre (cos, sin), see ring_xor
     int *counter = ctrl;
 
     // Warp w works on TMEM lane quarter q = w & 3 (the lanes it may access),
     // x half h, and half e of the 8-pixel groups / of the 16 rows of a block.
     const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1, e = w >> 3;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-    const int row = l & 15, xg = 2 * (w & 7) + (l >> 4), px0 = 4 * e;
+    // The thread owns pixels px0 .. px0 + 3 of its 8-pixel group; rows 8-15 take
+    // the other half than rows 0-7 so that the 8-byte stores of a half-warp into
+    // a core-matrix row cover all 32 banks.  In TMEM the thread's four pixels sit
+    // at the warp-uniform columns pc0 .. pc0 + 3.
+    const int row = l & 15, xg = 2 * (w & 7) + (l >> 4), pc0 = 4 * e, px0 = 4 * (e ^ (row >> 3));
 
     // ---- once per CTA: tensor memory, barriers ------------------------------------
     if (w == 0) {
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(kT, 1)
         // ---- region f -> tensor memory; in-image masks -------------------------------
         // The 8-pixel group (region row 16c + row, columns 8 xg .. 8 xg + 7) of
         // every chunk c lives in TMEM lane 32q + l at columns (2c + h)*24 +
-        // ch*8 + j; this thread owns its pixels j = px0 .. px0 + 3.
+        // ch*8 + pc0 + jj for pixel px0 + jj of this thread.
         uint32_t vmask = 0;  // bit 4c + jj: pixel px0 + jj inside the image
         uint32_t cmask = 0;  // bit jj: column is a centre (output) column
 #pragma unroll
@@ -321,7 +326,7 @@ __global__ void __launch_bounds__(kT, 1)
                     v[jj] = ((vmask >> (4 * c + jj)) & 1)
                                 ? __ldg(in + ch * plane + (size_t)(ry0 + 16 * c + row) * pitch + (rx0 + 8 * xg + px0 + jj))
                                 : 0.f;
-                tmem_st4(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8 + px0, v);
+                tmem_st4(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8 + pc0, v);
             }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -333,15 +338,26 @@ __global__ void __launch_bounds__(kT, 1)
             for (int j = 0; j < 8; ++j) acc[o][j] = 0.f;
 
         const int NCr = g.nc;  // 16-row chunks per term: ceil((BY + 2r) / 16) <= 8
+        uint8_t *const dstA = A1 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048 + 2 * px0;
+        // Ring columns of this thread's 4 pixels: the XOR depends on the ring row
+        // only through (row - r) & 7, a constant of the tile.
+        const int rx = ring_xor((row - r) & 7), cb = 8 * xg + px0 - r;
+        const int rcol0 = cb ^ rx, rcol1 = (cb + 1) ^ rx, rcol2 = (cb + 2) ^ rx, rcol3 = (cb + 3) ^ rx;
+        float nr0, nr1, nr2;  // frequency of the current term, radians per unit of f
+        auto load_nu = [&](int k) {
+            nr0 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k);
+            nr1 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k + 1);
+            nr2 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k + 2);
+        };
         const int S = K * NCr;
-        int pend_oc = -1, pend_sfirst = 0;
+        int pend_oc = -1, pend_slot = 0;
         const int kgring = g.Kw >> 3;
 
-        auto stage_A = [&](int s) {
-            const int k = s / NCr, c = s - k * NCr;
-            const float n0 = __ldg(nu_hi + 3 * k), n1 = __ldg(nu_hi + 3 * k + 1), n2 = __ldg(nu_hi + 3 * k + 2);
+        // A: channels of flat step s (chunk c of the term whose frequency is in
+        // nr0..nr2) into A1[s & 1]; slot16 = 16 s mod ringC.
+        auto stage_A = [&](int s, int c, int slot16) {
             float f0[4], f1[4], f2[4];
-            const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24 + px0;
+            const uint32_t fa = tmem + lane_base + kColF + (2 * c + h) * 24 + pc0;
             tmem_ld4(fa, f0);
             tmem_ld4(fa + 8, f1);
             tmem_ld4(fa + 16, f2);
@@ -357,10 +373,11 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int j = 2 * p + u;
-                    const float t = fmaf(n0, f0[j], fmaf(n1, f1[j], n2 * f2[j]));
-                    const float fr = t - rintf(t);
+                    // phase in radians; FP32 keeps its error near 1e-5 rad for |phase| <
+                    // 100, far below the 16-bit rounding of the channels
+                    const float t = fmaf(nr0, f0[j], fmaf(nr1, f1[j], nr2 * f2[j]));
                     float s_, c_;
-                    __sincosf(6.28318530717958647692f * fr, &s_, &c_);
+                    __sincosf(t, &s_, &c_);
                     const bool v = (vm >> j) & 1u;
                     cv[u] = v ? c_ : 0.f;
                     sv[u] = v ? s_ : 0.f;
@@ -392,47 +409,50 @@ __global__ void __launch_bounds__(kT, 1)
                     o[6][p] = bits(__hmul2(hs, g2));
                 }
             }
-            if (centre_row) {  // centre cos/sin for the combine, slot = flat region row mod ringC
-                const int slot = (16 * s + row) % g.ringC;
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-                    if ((cmask >> jj) & 1u) ring[ring_idx(slot, 8 * xg + px0 + jj - r)] = make_float2(csv[jj], snv[jj]);
+            if (centre_row) {  // centre cos/sin for the combine, ring row = flat output row mod ringC
+                int slot = slot16 + row - r;
+                if (slot < 0) slot += g.ringC;
+                float2 *rrow = ring + slot * kBX;
+                if (cmask & 1u) rrow[rcol0] = make_float2(csv[0], snv[0]);
+                if (cmask & 2u) rrow[rcol1] = make_float2(csv[1], snv[1]);
+                if (cmask & 4u) rrow[rcol2] = make_float2(csv[2], snv[2]);
+                if (cmask & 8u) rrow[rcol3] = make_float2(csv[3], snv[3]);
             }
-            // 4 pixels of one channel = the e-th half of a 16-byte core-matrix row
-            uint8_t *dst = A1 + (s & 1) * 32768 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048 + 8 * e;
+            // 4 pixels of one channel = half px0 / 4 of a 16-byte core-matrix row
+            uint8_t *dst = dstA + (s & 1) * 32768;
 #pragma unroll
             for (int ch = 0; ch < 8; ++ch)
                 *reinterpret_cast<uint2 *>(dst + ch * 4096) = make_uint2(o[ch][0], o[ch][1]);
         };
 
-        // C: combine output chunk oc (its window starts at flat step s_first)
-        auto stage_C = [&](int oc, int s_first) {
+        // C: combine output chunk oc; slot0 = ring row of its output row 16 oc + 8 e
+        // (a multiple of 8 at most ringC - 8: the 8 rows read never wrap)
+        auto stage_C = [&](int oc, int slot0) {
             float vc[8], vs[8];  // output rows 16 oc + 8 e + j of the cos / sin M-tile
             tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h) + 8 * e, vc);
             tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h + 1) + 8 * e, vs);
             tmem_wait_ld();
             const int x = 32 * h + l;
-            int slot = (16 * s_first + r + 8 * e) % g.ringC;  // flat region row of output row 16 oc + 8 e
+            const float2 *rrow = ring + slot0 * kBX;
 #pragma unroll
             for (int o = 0; o < NOC; ++o) {
                 if (o == oc) {
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
-                        const float2 cs = ring[ring_idx(slot, x)];
-                        if (++slot == g.ringC) slot = 0;
+                        const float2 cs = rrow[j * kBX + (x ^ ring_xor(j))];
                         acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
                     }
                 }
             }
         };
 
-        // X: D1 of flat step s -> A2 ring
-        auto stage_X = [&](int s) {
+        // X: D1 of a flat step -> A2 ring; kr16 = 16 s mod Kw
+        auto stage_X = [&](int kr16) {
             float v[16];  // output columns 32 h + 16 e .. + 15 of this (channel, row)
             tmem_ld16(tmem + lane_base + kColD1 + 32 * h + 16 * e, v);
             tmem_wait_ld();
             const int ch = 2 * q + (l >> 4), gsel = ch >> 2, p = ch & 3;
-            const int kr = (16 * s + row) % g.Kw;
+            const int kr = kr16 + row;
             uint8_t *base =
                 A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512 + 2 * e * 128;
 #pragma unroll
@@ -467,10 +487,8 @@ __global__ void __launch_bounds__(kT, 1)
         };
 
         // ---- prologue ------------------------------------------------------------------
-        stage_A(0);
-
-        // ---- prologue ------------------------------------------------------------------
-        stage_A(0);
+        load_nu(0);
+        stage_A(0, 0, 0);
         fence_async_smem();
         __syncthreads();
         if (w == 0 && l == 0) {
@@ -479,21 +497,31 @@ __global__ void __launch_bounds__(kT, 1)
         }
 
         // ---- pipeline ----------------------------------------------------------------------
-        for (int s = 0, c = 0; s < S; ++s, c = (c + 1 == NCr) ? 0 : c + 1) {
+        // Step s is chunk c of term k; slotS = 16 s mod ringC and krS = 16 s mod Kw
+        // are carried from step to step (no division in the loop), as are the
+        // chunk, term and slot of step s + 1 (cA, kA, slotA).
+        int c = 0, kA = 0, cA = 0, slotS = 0, krS = 0;
+        for (int s = 0; s < S; ++s) {
             const int oc = c - g.lag;
             const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
-            if (s + 1 < S) stage_A(s + 1);
+            if (++cA == NCr) {
+                cA = 0;
+                if (++kA < K) load_nu(kA);
+            }
+            int slotA = slotS + 16;
+            if (slotA >= g.ringC) slotA -= g.ringC;
+            if (s + 1 < S) stage_A(s + 1, cA, slotA);
             if (pend_oc >= 0) {
                 if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
                 ph2 ^= 1;
                 fence_after();
-                stage_C(pend_oc, pend_sfirst);
+                stage_C(pend_oc, pend_slot);
                 pend_oc = -1;
             }
             if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
             ph1 ^= 1;
             fence_after();
-            stage_X(s);
+            stage_X(krS);
             fence_before();
             fence_async_smem();
             if (timed_out) abort_s = 1;
@@ -510,14 +538,22 @@ __global__ void __launch_bounds__(kT, 1)
             __syncwarp();
             if (do_m2) {
                 pend_oc = oc;
-                pend_sfirst = s - g.lag;
+                // flat output row 16 (s - lag) + 8 e, mod ringC (16 lag < ringC)
+                int sl = slotS - 16 * g.lag + 8 * e;
+                if (sl < 0) sl += g.ringC;
+                if (sl >= g.ringC) sl -= g.ringC;
+                pend_slot = sl;
             }
+            c = cA;
+            slotS = slotA;
+            krS += 16;
+            if (krS == g.Kw) krS = 0;
         }
         if (pend_oc >= 0) {
             if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
             ph2 ^= 1;
             fence_after();
-            stage_C(pend_oc, pend_sfirst);
+            stage_C(pend_oc, pend_slot);
         }
         if (timed_out) abort_s = 1;
         fence_before();
