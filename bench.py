@@ -476,6 +476,58 @@ def run_serve(args):
     return 0
 
 
+def run_sigma_sweep(args):
+    """Run time against sigma_s, the analogue of Table 1 (Section 4): RGB,
+    sigma_r = 40, N = 10, T = 300, sigma_s in {1, 2, 3, 4, 5, 10}, on a
+    512 x 512 image (the paper's Peppers size; synthetic stand-in: 16 Voronoi
+    cells plus noise of std 10) and on the 3840 x 2160 image of the headline
+    workload.  Device time of one bf_filter per image (CUDA events, median of
+    `--steps` launches after 3 warm-ups), for the tensor-core and the FP32
+    paths."""
+    import torch
+    from paper_1605_02164_gb300 import bf
+    from paper_1605_02164_gb300 import build as B
+    B.build()
+    torch.cuda.set_device(0)
+    sp = torch.cuda.current_stream().cuda_stream
+    C = np.diag([40.0 ** 2] * 3)
+    reps = max(3, args.steps)
+
+    def median_ms(plan, x, y, v):
+        for _ in range(3):
+            bf.bf_filter(plan, x.data_ptr(), y.data_ptr(), x.shape[1], x.shape[2], x.stride(1), v, sp)
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bf.bf_filter(plan, x.data_ptr(), y.data_ptr(), x.shape[1], x.shape[2], x.stride(1), v, sp)
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    rows = []
+    for H, W in ((512, 512), (2160, 3840)):
+        f = synth.voronoi_image(H, W, 3, 16, 10.0, seed=args.seed + H)
+        x = bf.to_pitched(f)
+        y = bf.pitched_empty(3, H, W)
+        for s in (1.0, 2.0, 3.0, 4.0, 5.0, 10.0):
+            p = bf.bf_plan(3, C, s, 10, 300, args.seed + int(10 * s))
+            row = {"H": H, "W": W, "sigma_s": s, "r": p.r}
+            for name in (args.variant, "fp32"):
+                ms = median_ms(p, x, y, bf.VARIANTS[name])
+                row[f"{name}_ms"] = ms
+                row[f"{name}_mpx"] = H * W / ms / 1e3
+            rows.append(row)
+    if bf.bf_last_status(sp) != bf.BF_OK:
+        raise RuntimeError("device status after the sweep")
+    line = {"metric": "ms per image vs sigma_s (RGB, sigma_r=40, N=10, T=300)", "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": reps, "dtype": args.variant, "data": "synthetic",
+            "config": {"workload": "sigma_sweep_rgb_512x512_and_3840x2160_sr40_N10_T300"}, "rows": rows}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -483,7 +535,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="fp16tc", choices=["fp32", "fp16tc", "bf16tc"])
-    ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS) + ["batch", "serve"])
+    ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS) + ["batch", "serve", "sigma-sweep"])
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=0.25)
     ap.add_argument("--seed", type=int, default=3000)
@@ -500,6 +552,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "sigma-sweep":
+        return run_sigma_sweep(args)
     return run_ours(args)
 
 

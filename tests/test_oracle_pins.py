@@ -384,3 +384,24 @@ def test_fig5_error_decreases_with_T_and_is_subpixel():
                           for m in range(4)])
     assert res[25] > res[100] > res[400]
     assert res[400] < 1.0
+
+
+def test_fig5_variance_falls_as_one_over_T_and_saturates_in_N():
+    """Section 4 / Fig. 5: the MC error of Algorithm 1 behaves as variance / T
+    (Prop. 2 makes the estimator an average of T iid terms, so its variance is
+    1/T of one term's), and for a fixed large T the MSE hardly changes from
+    N = 10 to N = 20 (the paper's saturation in N).  Checked on a 64 x 64
+    synthetic stand-in at sigma_s = 1, sigma_r = 30, 4 seeds per point."""
+    d = 3
+    f = synth.voronoi_image(64, 64, d, 8, 10.0, seed=1001).astype(np.float64)
+    C = np.diag([30.0 ** 2] * d)
+    A = O.direct(f, 1.0, C)
+    Wm = O.whiten(C, 0)
+    m = {}
+    for N in (10, 20):
+        for T in (40, 640):
+            m[N, T] = np.mean([O.mse(A, O.mcsf(f, 1.0, Wm, N, O.sample_Y(d, N, T, 60_000 + 17 * T + N + k))["S"])
+                               for k in range(4)])
+    slope = math.log(m[10, 640] / m[10, 40]) / math.log(16.0)
+    assert -1.3 < slope < -0.7, slope
+    assert abs(10 * math.log10(m[20, 640] / m[10, 640])) < 1.5
