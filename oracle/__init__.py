@@ -72,6 +72,8 @@ def _load():
                                           ctypes.c_int, ip, dp, dp, dp]
         lib.orc_rc_direct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
                                       ctypes.c_int, dp, ctypes.c_int, dp, dp]
+        lib.orc_rgb_to_lab.argtypes = [ctypes.c_int, dp, dp]
+        lib.orc_lab_to_rgb.argtypes = [ctypes.c_int, dp, dp]
         _lib = lib
         return lib
 
@@ -256,6 +258,27 @@ def mcsf_exhaustive(f, sigma_s: float, Wm, N: int, r: int | None = None) -> dict
     d = _img(f).shape[0]
     Y, w = exhaustive_Y(d, N)
     return mcsf(f, sigma_s, Wm, N, Y, weights=w, r=r)
+
+
+def rgb_to_lab(f):
+    """sRGB on the 0..255 scale (3, H, W) -> CIE 1976 (L*, a*, b*), the colour
+    transform of Section 4's Lab experiment (Fig. 4); D65 white, no clipping."""
+    f = _img(f)
+    assert f.shape[0] == 3
+    out = np.zeros_like(f)
+    if _load().orc_rgb_to_lab(f[0].size, _dp(f), _dp(out)):
+        raise ValueError("orc_rgb_to_lab failed")
+    return out
+
+
+def lab_to_rgb(lab):
+    """Inverse of rgb_to_lab (no clipping)."""
+    lab = _img(lab)
+    assert lab.shape[0] == 3
+    out = np.zeros_like(lab)
+    if _load().orc_lab_to_rgb(lab[0].size, _dp(lab), _dp(out)):
+        raise ValueError("orc_lab_to_rgb failed")
+    return out
 
 
 # ----------------------------------------------------------------------------

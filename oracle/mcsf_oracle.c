@@ -24,6 +24,8 @@
  *   orc_mcsf              shiftable MC filter, part B1         [Algorithm 1, Eqs. numerator, denom]
  *   orc_mcsf_pairwise     same estimator, pairwise form, B2    [Eqs. bigExp, smallExp]
  *   orc_rc_direct         raised-cosine kernel filter, part C1 [Eq. approx]
+ *   orc_rgb_to_lab,       sRGB (0..255) <-> CIE 1976 L*a*b*, the colour transform
+ *   orc_lab_to_rgb        around the filter in Section 4 (Fig. 4)
  *
  * Readings of points the paper leaves open (boundary, window, real part,
  * sampling) are stated beside the code that takes them.
@@ -535,6 +537,76 @@ int orc_rc_direct(int d, int H, int W, const double *f, double sigma_s, int r,
             }
             for (int c = 0; c < d; ++c) out[c * HW + (size_t)y * W + x] = num[c] / Z;
             if (Zout) Zout[(size_t)y * W + x] = Z;
+        }
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* CIE-Lab colour transform used around the filter (Section 4, Fig. 4).     */
+/* ------------------------------------------------------------------------ */
+
+/* The paper filters House in CIE-Lab (citing Wyszecki & Stiles) without naming
+ * the RGB space.  Reading: the RGB values are sRGB on the 0..255 scale
+ * (IEC 61966-2-1: piecewise transfer function and its D65 RGB -> XYZ matrix,
+ * given there to four decimals), the white point is the XYZ of RGB white (the
+ * matrix's row sums), and L*a*b* is CIE 1976.  No clipping either way, so
+ * out-of-gamut values produced by the filter survive the round trip. */
+static const double SRGB_TO_XYZ[9] = {0.4124, 0.3576, 0.1805,   /* X */
+                                      0.2126, 0.7152, 0.0722,   /* Y */
+                                      0.0193, 0.1192, 0.9505};  /* Z */
+
+static double srgb_decode(double v) { /* encoded 0..1 -> linear */
+    return (v <= 0.04045) ? v / 12.92 : pow((v + 0.055) / 1.055, 2.4);
+}
+static double srgb_encode(double u) { /* linear -> encoded 0..1 */
+    return (u <= 0.0031308) ? 12.92 * u : 1.055 * pow(u, 1.0 / 2.4) - 0.055;
+}
+/* CIE 1976 companding with delta = 6/29: cube root above delta^3, the tangent
+ * line t / (3 delta^2) + 4/29 below it; lab_finv is its inverse. */
+static double lab_f(double t) {
+    const double dl = 6.0 / 29.0;
+    return (t > dl * dl * dl) ? cbrt(t) : t / (3.0 * dl * dl) + 4.0 / 29.0;
+}
+static double lab_finv(double t) {
+    const double dl = 6.0 / 29.0;
+    return (t > dl) ? t * t * t : 3.0 * dl * dl * (t - 4.0 / 29.0);
+}
+
+/* rgb, lab: planar 3 x n (channel-major); 0..255 sRGB <-> (L*, a*, b*). */
+int orc_rgb_to_lab(int n, const double *rgb, double *lab) {
+    if (n < 0) return ORC_ERR_ARG;
+    double white[3];
+    for (int i = 0; i < 3; ++i) white[i] = SRGB_TO_XYZ[3 * i] + SRGB_TO_XYZ[3 * i + 1] + SRGB_TO_XYZ[3 * i + 2];
+    for (int p = 0; p < n; ++p) {
+        double lin[3], fx[3];
+        for (int c = 0; c < 3; ++c) lin[c] = srgb_decode(rgb[(size_t)c * n + p] / 255.0);
+        for (int i = 0; i < 3; ++i) {
+            double xyz = 0.0;
+            for (int c = 0; c < 3; ++c) xyz += SRGB_TO_XYZ[3 * i + c] * lin[c];
+            fx[i] = lab_f(xyz / white[i]);
+        }
+        lab[p] = 116.0 * fx[1] - 16.0;
+        lab[(size_t)n + p] = 500.0 * (fx[0] - fx[1]);
+        lab[(size_t)2 * n + p] = 200.0 * (fx[1] - fx[2]);
+    }
+    return ORC_OK;
+}
+
+int orc_lab_to_rgb(int n, const double *lab, double *rgb) {
+    if (n < 0) return ORC_ERR_ARG;
+    double white[3], Minv[9];
+    for (int i = 0; i < 3; ++i) white[i] = SRGB_TO_XYZ[3 * i] + SRGB_TO_XYZ[3 * i + 1] + SRGB_TO_XYZ[3 * i + 2];
+    if (invert(3, SRGB_TO_XYZ, Minv) != ORC_OK) return ORC_ERR_ARG;
+    for (int p = 0; p < n; ++p) {
+        const double fy = (lab[p] + 16.0) / 116.0;
+        const double f3[3] = {fy + lab[(size_t)n + p] / 500.0, fy, fy - lab[(size_t)2 * n + p] / 200.0};
+        double xyz[3];
+        for (int i = 0; i < 3; ++i) xyz[i] = white[i] * lab_finv(f3[i]);
+        for (int c = 0; c < 3; ++c) {
+            double u = 0.0;
+            for (int i = 0; i < 3; ++i) u += Minv[3 * c + i] * xyz[i];
+            rgb[(size_t)c * n + p] = 255.0 * srgb_encode(u);
         }
     }
     return ORC_OK;

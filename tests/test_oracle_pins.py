@@ -405,3 +405,52 @@ def test_fig5_variance_falls_as_one_over_T_and_saturates_in_N():
     slope = math.log(m[10, 640] / m[10, 40]) / math.log(16.0)
     assert -1.3 < slope < -0.7, slope
     assert abs(10 * math.log10(m[20, 640] / m[10, 640])) < 1.5
+
+
+# ---------------------------------------------------------------- CIE-Lab ---
+
+def _lab_of(rgb):
+    return O.rgb_to_lab(np.asarray(rgb, np.float64).T.reshape(3, 1, -1))[:, 0, :].T
+
+
+def test_lab_tabulated_colours():
+    """Section 4 (Fig. 4) filters in CIE-Lab.  The transform is pinned to the
+    tabulated L*a*b* of the sRGB primaries, secondaries and mid grey
+    (tests/golden/srgb_lab_reference.json, sources cited there)."""
+    g = json.load(open(os.path.join(GOLD, "srgb_lab_reference.json")))
+    names = list(g["colours"])
+    got = _lab_of([g["colours"][k]["rgb"] for k in names])
+    for k, v in zip(names, got):
+        assert np.abs(v - np.array(g["colours"][k]["lab"])).max() < g["tolerance"], (k, v)
+
+
+def test_lab_white_black_grey_axis():
+    """White is (100, 0, 0) and black (0, 0, 0) by construction of the white
+    point; every grey has a* = b* = 0 and L* increases with the grey level."""
+    w, k = _lab_of([[255, 255, 255], [0, 0, 0]])
+    assert np.abs(w - [100, 0, 0]).max() < 1e-12 and np.abs(k).max() < 1e-12
+    grey = _lab_of([[v, v, v] for v in np.linspace(0, 255, 52)])
+    assert np.abs(grey[:, 1:]).max() < 1e-12
+    assert np.all(np.diff(grey[:, 0]) > 0)
+
+
+def test_lab_round_trip_and_continuity():
+    """lab_to_rgb inverts rgb_to_lab (also outside [0, 255], no clipping), and
+    both piecewise definitions meet at their break points: the sRGB one at
+    0.04045 up to the ~1e-6 step its published rounded constants leave, the
+    CIE one at Y/Yn = (6/29)^3, i.e. L* = 116 (6/29) - 16 = 8."""
+    rng = np.random.default_rng(5)
+    f = rng.uniform(-20, 275, (3, 17, 23))
+    assert np.abs(O.lab_to_rgb(O.rgb_to_lab(f)) - f).max() < 1e-9
+    v = 0.04045 * 255
+    a, b = _lab_of([[v - 1e-9] * 3, [v + 1e-9] * 3])
+    assert abs(a[0] - b[0]) < 1e-5
+    lo, hi = 0.0, 255.0  # grey level where L* crosses 8, by bisection
+    for _ in range(80):
+        mid = (lo + hi) / 2
+        if _lab_of([[mid] * 3])[0, 0] < 116 * (6 / 29) - 16:
+            lo = mid
+        else:
+            hi = mid
+    a, b = _lab_of([[lo - 1e-7] * 3, [lo + 1e-7] * 3])
+    assert abs(a[0] - b[0]) < 1e-5
