@@ -187,6 +187,22 @@ int bf_filter_batch_noalloc(const bf_item *items, int n, int variant, void *stre
 int bf_filter_host(bf_plan_t plan, const float *in_host, float *out_host, int H, int W, int variant,
                    void *stream);
 
+/*
+ * bf_rgb_to_lab / bf_lab_to_rgb -- colour transforms for filtering in CIE-Lab,
+ * as the paper does for its House example (Section 4, Fig. 4): convert, filter
+ * the Lab image with a plan whose C is in Lab units, convert back.
+ * The RGB side is sRGB on the 0..255 scale (IEC 61966-2-1 transfer function
+ * and D65 matrix), the Lab side CIE 1976 (L*, a*, b*) with the white point of
+ * RGB white; nothing is clipped in either direction.
+ *   in, out  device pointers, planar [3][H][pitch] FP32, 16-byte aligned
+ *            (else BF_ERR_ALIGN); in == out (in place) is allowed, any other
+ *            overlap is BF_ERR_ARG.
+ *   H, W     image size (0 is a no-op); pitch >= W, pitch % 4 == 0.
+ * Asynchronous on `stream`; one elementwise kernel each.
+ */
+int bf_rgb_to_lab(const float *in, float *out, int H, int W, int pitch, void *stream);
+int bf_lab_to_rgb(const float *in, float *out, int H, int W, int pitch, void *stream);
+
 /* Status word of the library's device-side guards (bounded waits, tile-queue
  * consistency) for work issued on `stream`; synchronises the stream, returns
  * BF_OK or the first BF_ERR_* recorded, and clears it. */

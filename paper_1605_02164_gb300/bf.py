@@ -84,6 +84,8 @@ def _load():
         lib.bf_filter_batch.argtypes = [ctypes.POINTER(bf_item), i, i, vp]
         lib.bf_filter_batch_noalloc.argtypes = [ctypes.POINTER(bf_item), i, i, vp]
         lib.bf_filter_host.argtypes = [vp, vp, vp, i, i, i, vp]
+        lib.bf_rgb_to_lab.argtypes = [vp, vp, i, i, i, vp]
+        lib.bf_lab_to_rgb.argtypes = [vp, vp, i, i, i, vp]
         lib.bf_last_status.argtypes = [vp]
         lib.bf_error_string.argtypes = [i]
         lib.bf_error_string.restype = ctypes.c_char_p
@@ -200,6 +202,18 @@ def bf_filter_host(plan: Plan, in_host: np.ndarray, out_host: np.ndarray | None 
     return out_host
 
 
+def bf_rgb_to_lab(in_ptr: int, out_ptr: int, H: int, W: int, pitch: int, stream: int = 0):
+    """sRGB (0..255) -> CIE 1976 L*a*b*, planar [3][H][pitch] device buffers (in place allowed)."""
+    _check(_load().bf_rgb_to_lab(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(H), int(W), int(pitch),
+                                 ctypes.c_void_p(stream)), "bf_rgb_to_lab")
+
+
+def bf_lab_to_rgb(in_ptr: int, out_ptr: int, H: int, W: int, pitch: int, stream: int = 0):
+    """CIE 1976 L*a*b* -> sRGB (0..255), planar [3][H][pitch] device buffers (in place allowed)."""
+    _check(_load().bf_lab_to_rgb(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(H), int(W), int(pitch),
+                                 ctypes.c_void_p(stream)), "bf_lab_to_rgb")
+
+
 def bf_last_status(stream: int = 0) -> int:
     return int(_load().bf_last_status(ctypes.c_void_p(stream)))
 
@@ -231,6 +245,27 @@ def filter_tensor(plan: Plan, x, variant: int = BF_FP32, out=None, stream=None):
         out = torch.empty_strided(x.shape, x.stride(), dtype=x.dtype, device=x.device)
     bf_filter(plan, x.data_ptr(), out.data_ptr(), H, W, pitch, variant, _stream_ptr(stream))
     return out
+
+
+def convert_tensor(x, to_lab: bool, out=None, stream=None):
+    """bf_rgb_to_lab / bf_lab_to_rgb on a CUDA float32 (3, H, W) pitched tensor."""
+    import torch
+    assert x.is_cuda and x.dtype == torch.float32 and x.dim() == 3 and x.shape[0] == 3 and x.stride(2) == 1
+    _, H, W = x.shape
+    assert x.stride(0) == H * x.stride(1), "planes must be contiguous [3][H][pitch]"
+    if out is None:
+        out = torch.empty_strided(x.shape, x.stride(), dtype=x.dtype, device=x.device)
+    fn = bf_rgb_to_lab if to_lab else bf_lab_to_rgb
+    fn(x.data_ptr(), out.data_ptr(), H, W, x.stride(1), _stream_ptr(stream))
+    return out
+
+
+def filter_lab_tensor(plan: Plan, x, variant: int = BF_FP32, out=None, stream=None):
+    """Filter an sRGB image in CIE-Lab (Section 4, Fig. 4): convert, filter
+    with `plan` (its C in Lab units), convert back.  Returns ``out`` (RGB)."""
+    lab = convert_tensor(x, True, stream=stream)
+    lab_out = filter_tensor(plan, lab, variant, stream=stream)
+    return convert_tensor(lab_out, False, out=out, stream=stream)
 
 
 def pitched_empty(d: int, H: int, W: int, device="cuda"):

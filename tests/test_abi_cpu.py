@@ -64,3 +64,18 @@ def test_host_side_argument_checks(lib):
     assert L.bf_plan_destroy(None) == bf.BF_ERR_ARG
     assert L.bf_filter_batch(None, -1, 0, None) == bf.BF_ERR_ARG
     assert L.bf_filter_batch(None, 0, 0, None) == bf.BF_OK
+
+
+def test_colour_transform_argument_checks(lib):
+    """bf_rgb_to_lab / bf_lab_to_rgb reject bad arguments before any CUDA call."""
+    from paper_1605_02164_gb300 import bf
+    L = bf.lib()
+    vp = ctypes.c_void_p
+    for fn in (L.bf_rgb_to_lab, L.bf_lab_to_rgb):
+        assert fn(None, None, 0, 5, 8, None) == bf.BF_OK          # empty image: no-op
+        assert fn(None, None, 4, 5, 8, None) == bf.BF_ERR_ARG      # null buffers
+        assert fn(vp(0x10000), vp(0x20000), 4, 9, 8, None) == bf.BF_ERR_ARG   # pitch < W
+        assert fn(vp(0x10000), vp(0x20000), -1, 4, 8, None) == bf.BF_ERR_ARG
+        assert fn(vp(0x10004), vp(0x20000), 4, 5, 8, None) == bf.BF_ERR_ALIGN
+        assert fn(vp(0x10000), vp(0x20000), 4, 5, 6, None) == bf.BF_ERR_ALIGN  # pitch % 4
+        assert fn(vp(0x10000), vp(0x10010), 4, 5, 8, None) == bf.BF_ERR_ARG   # partial overlap
