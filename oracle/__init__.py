@@ -72,6 +72,11 @@ def _load():
                                           ctypes.c_int, ip, dp, dp, dp]
         lib.orc_rc_direct.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
                                       ctypes.c_int, dp, ctypes.c_int, dp, dp]
+        lib.orc_deriche_blur.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp]
+        lib.orc_mcsf_deriche.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp,
+                                         ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp]
+        lib.orc_mcsf_deriche_pairwise.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                                  dp, ctypes.c_int, ctypes.c_int, ip, ctypes.c_int, ip, dp]
         lib.orc_rgb_to_lab.argtypes = [ctypes.c_int, dp, dp]
         lib.orc_lab_to_rgb.argtypes = [ctypes.c_int, dp, dp]
         _lib = lib
@@ -258,6 +263,46 @@ def mcsf_exhaustive(f, sigma_s: float, Wm, N: int, r: int | None = None) -> dict
     d = _img(f).shape[0]
     Y, w = exhaustive_Y(d, N)
     return mcsf(f, sigma_s, Wm, N, Y, weights=w, r=r)
+
+
+def deriche_blur(img, sigma: float):
+    """Recursive (Deriche) Gaussian blur of a real (H, W) image, zero outside:
+    the O(1)-in-sigma convolution of Section 3."""
+    img = _f64(img)
+    assert img.ndim == 2
+    out = np.zeros_like(img)
+    if _load().orc_deriche_blur(img.shape[0], img.shape[1], _dp(img), float(sigma), _dp(out)):
+        raise ValueError("orc_deriche_blur failed")
+    return out
+
+
+def mcsf_deriche(f, sigma_s: float, Wm, N: int, Y, weights=None) -> dict:
+    """Algorithm 1 with the recursive blur: S = Re P / Re Z (dict S, Pre, Zre)."""
+    f = _img(f)
+    d, H, W = f.shape
+    Y = np.ascontiguousarray(Y, np.int32)
+    K = Y.shape[0]
+    S, P, Z = np.zeros_like(f), np.zeros_like(f), np.zeros((H, W))
+    wts = None if weights is None else _f64(weights)
+    rc = _load().orc_mcsf_deriche(d, H, W, _dp(f), float(sigma_s), _dp(_f64(Wm)), N, K, _ip(Y), _dp(wts),
+                                  _dp(S), _dp(P), _dp(Z))
+    if rc:
+        raise ValueError(f"orc_mcsf_deriche failed: {rc}")
+    return {"S": S, "Pre": P, "Zre": Z}
+
+
+def mcsf_deriche_pairwise(f, sigma_s: float, Wm, N: int, Y, pix) -> np.ndarray:
+    """Pairwise form with the closed-form recursive kernel at pixels pix (n, 2) -> (n, d)."""
+    f = _img(f)
+    d, H, W = f.shape
+    Y = np.ascontiguousarray(Y, np.int32)
+    pix = np.ascontiguousarray(pix, np.int32)
+    out = np.zeros((pix.shape[0], d))
+    rc = _load().orc_mcsf_deriche_pairwise(d, H, W, _dp(f), float(sigma_s), _dp(_f64(Wm)), N, Y.shape[0], _ip(Y),
+                                           pix.shape[0], _ip(pix), _dp(out))
+    if rc:
+        raise ValueError(f"orc_mcsf_deriche_pairwise failed: {rc}")
+    return out
 
 
 def rgb_to_lab(f):

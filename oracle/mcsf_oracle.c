@@ -24,6 +24,9 @@
  *   orc_mcsf              shiftable MC filter, part B1         [Algorithm 1, Eqs. numerator, denom]
  *   orc_mcsf_pairwise     same estimator, pairwise form, B2    [Eqs. bigExp, smallExp]
  *   orc_rc_direct         raised-cosine kernel filter, part C1 [Eq. approx]
+ *   orc_deriche_blur      recursive (Deriche) Gaussian blur    [Section 3, convolution in O(1)]
+ *   orc_mcsf_deriche      Algorithm 1 with the recursive blur  [same]
+ *   orc_mcsf_deriche_pairwise  its pairwise form with the closed-form kernel
  *   orc_rgb_to_lab,       sRGB (0..255) <-> CIE 1976 L*a*b*, the colour transform
  *   orc_lab_to_rgb        around the filter in Section 4 (Fig. 4)
  *
@@ -609,5 +612,230 @@ int orc_lab_to_rgb(int n, const double *lab, double *rgb) {
             rgb[(size_t)c * n + p] = 255.0 * srgb_encode(u);
         }
     }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Recursive (Deriche) Gaussian: the O(1)-in-sigma_s convolution the paper   */
+/* names for Algorithm 1's convolution step (Section 3, citing Deriche 1993).*/
+/* ------------------------------------------------------------------------ */
+
+/* Deriche approximates the unnormalised Gaussian exp(-x^2 / 2 sigma^2), x >= 0,
+ * by two damped sinusoids in x / sigma,
+ *   h(x) = (a0 cos(w0 x/s) + a1 sin(w0 x/s)) e^{-b0 x/s}
+ *        + (c0 cos(w1 x/s) + c1 sin(w1 x/s)) e^{-b1 x/s},
+ * with his published fit a0 = 1.680, a1 = 3.735, b0 = 1.783, w0 = 0.6318,
+ * c0 = -0.6803, c1 = -0.2598, b1 = 1.723, w1 = 1.997, and filters with h(|n|)
+ * as the sum of a causal (n >= 0) and an anticausal (n <= -1) recursion.
+ * The coefficients below come from the z-transform of each sampled term:
+ *   e^{-beta n}(a cos(om n) + c sin(om n))  ->
+ *   (a + (c sin om - a cos om) e^{-beta} z^-1) / (1 - 2 e^{-beta} cos om z^-1 + e^{-2 beta} z^-2),
+ * summed over the two terms (numerator order 3, denominator order 4).  The
+ * anticausal part is h(m), m >= 1, run backwards: numerator m_i = n_i - n_0 d_i.
+ * Zero state at both ends of a line: inputs outside the image are zero, the
+ * same truncation reading as the windowed filter (R5).  The infinite support
+ * makes it a different filter from the 3-sigma window: this is its own
+ * oracle variant. */
+typedef struct {
+    double n[4];  /* causal numerator n_0..n_3 */
+    double m[5];  /* anticausal numerator m_1..m_4 (m[0] unused) */
+    double dd[5]; /* denominator d_1..d_4 (dd[0] unused) */
+} deriche_coef;
+
+static const double DERICHE_FIT[8] = {1.680, 3.735, 1.783, 0.6318, -0.6803, -0.2598, 1.723, 1.997};
+
+static void deriche_coefficients(double sigma, deriche_coef *k) {
+    const double a0 = DERICHE_FIT[0], a1 = DERICHE_FIT[1], be0 = DERICHE_FIT[2] / sigma, om0 = DERICHE_FIT[3] / sigma;
+    const double c0 = DERICHE_FIT[4], c1 = DERICHE_FIT[5], be1 = DERICHE_FIT[6] / sigma, om1 = DERICHE_FIT[7] / sigma;
+    /* second-order denominators 1 + p_i1 z^-1 + p_i2 z^-2 and numerators q_i0 + q_i1 z^-1 */
+    const double p01 = -2.0 * exp(-be0) * cos(om0), p02 = exp(-2.0 * be0);
+    const double p11 = -2.0 * exp(-be1) * cos(om1), p12 = exp(-2.0 * be1);
+    const double q00 = a0, q01 = (a1 * sin(om0) - a0 * cos(om0)) * exp(-be0);
+    const double q10 = c0, q11 = (c1 * sin(om1) - c0 * cos(om1)) * exp(-be1);
+    /* numerator q0 p1 + q1 p0 */
+    k->n[0] = q00 + q10;
+    k->n[1] = q00 * p11 + q01 + q10 * p01 + q11;
+    k->n[2] = q00 * p12 + q01 * p11 + q10 * p02 + q11 * p01;
+    k->n[3] = q01 * p12 + q11 * p02;
+    /* denominator p0 p1 */
+    k->dd[0] = 1.0;
+    k->dd[1] = p01 + p11;
+    k->dd[2] = p02 + p12 + p01 * p11;
+    k->dd[3] = p01 * p12 + p11 * p02;
+    k->dd[4] = p02 * p12;
+    k->m[0] = 0.0;
+    for (int i = 1; i <= 3; ++i) k->m[i] = k->n[i] - k->n[0] * k->dd[i];
+    k->m[4] = -k->n[0] * k->dd[4];
+}
+
+/* out[i] = sum_j h(|i - j|) in[j] over the line (length n, element stride st):
+ * causal recursion left to right plus anticausal recursion right to left. */
+static void deriche_line(const double complex *in, double complex *out, int n, size_t st, const deriche_coef *k,
+                         double complex *ya) {
+    double complex yp[4] = {0, 0, 0, 0}, xp[3] = {0, 0, 0}; /* y(i-1..i-4), x(i-1..i-3) */
+    for (int i = 0; i < n; ++i) {
+        const double complex x = in[(size_t)i * st];
+        const double complex y = k->n[0] * x + k->n[1] * xp[0] + k->n[2] * xp[1] + k->n[3] * xp[2] -
+                                 k->dd[1] * yp[0] - k->dd[2] * yp[1] - k->dd[3] * yp[2] - k->dd[4] * yp[3];
+        xp[2] = xp[1]; xp[1] = xp[0]; xp[0] = x;
+        yp[3] = yp[2]; yp[2] = yp[1]; yp[1] = yp[0]; yp[0] = y;
+        out[(size_t)i * st] = y;
+    }
+    double complex ym[4] = {0, 0, 0, 0}, xm[4] = {0, 0, 0, 0}; /* y(i+1..i+4), x(i+1..i+4) */
+    for (int i = n - 1; i >= 0; --i) {
+        const double complex y = k->m[1] * xm[0] + k->m[2] * xm[1] + k->m[3] * xm[2] + k->m[4] * xm[3] -
+                                 k->dd[1] * ym[0] - k->dd[2] * ym[1] - k->dd[3] * ym[2] - k->dd[4] * ym[3];
+        xm[3] = xm[2]; xm[2] = xm[1]; xm[1] = xm[0]; xm[0] = in[(size_t)i * st];
+        ym[3] = ym[2]; ym[2] = ym[1]; ym[1] = ym[0]; ym[0] = y;
+        ya[i] = y;
+    }
+    for (int i = 0; i < n; ++i) out[(size_t)i * st] += ya[i];
+}
+
+/* Separable 2-D recursive blur: rows, then columns. */
+static int deriche_conv(const double complex *in, double complex *tmp, double complex *out, int H, int W,
+                        const deriche_coef *k) {
+    int fail = 0;
+#pragma omp parallel
+    {
+        double complex *ya = malloc(sizeof(double complex) * (size_t)(H > W ? H : W));
+        if (!ya) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(static)
+        for (int y = 0; y < H; ++y)
+            if (ya) deriche_line(in + (size_t)y * W, tmp + (size_t)y * W, W, 1, k, ya);
+#pragma omp for schedule(static)
+        for (int x = 0; x < W; ++x)
+            if (ya) deriche_line(tmp + x, out + x, H, (size_t)W, k, ya);
+        free(ya);
+    }
+    return fail ? ORC_ERR_NOMEM : ORC_OK;
+}
+
+/* The recursive blur of a real single-channel image (H x W). */
+int orc_deriche_blur(int H, int W, const double *in, double sigma, double *out) {
+    if (H < 0 || W < 0 || !(sigma > 0)) return ORC_ERR_ARG;
+    const size_t HW = (size_t)H * W;
+    if (HW == 0) return ORC_OK;
+    deriche_coef k;
+    deriche_coefficients(sigma, &k);
+    double complex *a = malloc(sizeof(double complex) * HW), *t = malloc(sizeof(double complex) * HW),
+                   *b = malloc(sizeof(double complex) * HW);
+    int rc = (a && t && b) ? ORC_OK : ORC_ERR_NOMEM;
+    if (rc == ORC_OK) {
+        for (size_t p = 0; p < HW; ++p) a[p] = in[p];
+        rc = deriche_conv(a, t, b, H, W, &k);
+        if (rc == ORC_OK)
+            for (size_t p = 0; p < HW; ++p) out[p] = creal(b[p]);
+    }
+    free(a); free(t); free(b);
+    return rc;
+}
+
+/* Algorithm 1 with the recursive blur in place of the windowed one: the same
+ * steps as orc_mcsf (g = W f, H_t, G_t, both blurred, combined with conj(H_t),
+ * S = Re P / Re Z), each convolution being deriche_conv.  Outputs as orc_mcsf. */
+int orc_mcsf_deriche(int d, int H, int W, const double *f, double sigma_s, const double *Wm, int N, int K,
+                     const int32_t *Y, const double *weights, double *out, double *Pre, double *Zre) {
+    if (d < 1 || d > 8 || H < 0 || W < 0 || N < 1 || K < 1 || !(sigma_s > 0)) return ORC_ERR_ARG;
+    const size_t HW = (size_t)H * (size_t)W;
+    if (HW == 0) return ORC_OK;
+    deriche_coef kc;
+    deriche_coefficients(sigma_s, &kc);
+    const double gamma = 1.0 / sqrt((double)N);
+    double *g = malloc(sizeof(double) * HW * d);
+    double complex *Hc = malloc(sizeof(double complex) * HW);
+    double complex *G = malloc(sizeof(double complex) * HW * d);
+    double complex *tmp = malloc(sizeof(double complex) * HW);
+    double complex *bar = malloc(sizeof(double complex) * HW);
+    double complex *P = calloc(HW * d, sizeof(double complex));
+    double complex *Zc = calloc(HW, sizeof(double complex));
+    int rc = (g && Hc && G && tmp && bar && P && Zc) ? ORC_OK : ORC_ERR_NOMEM;
+    if (rc == ORC_OK) {
+#pragma omp parallel for schedule(static)
+        for (long long p = 0; p < (long long)HW; ++p)
+            for (int k = 0; k < d; ++k) {
+                double s = 0.0;
+                for (int c = 0; c < d; ++c) s += Wm[k * d + c] * f[c * HW + p];
+                g[k * HW + p] = s;
+            }
+        for (int t = 0; t < K && rc == ORC_OK; ++t) {
+            const double wt = weights ? weights[t] : 1.0 / (double)K;
+#pragma omp parallel for schedule(static)
+            for (long long p = 0; p < (long long)HW; ++p) {
+                double complex h = 1.0;
+                for (int k = 0; k < d; ++k) h *= cexp(I * ((double)Y[t * d + k] * gamma * g[k * HW + p]));
+                Hc[p] = h;
+                for (int c = 0; c < d; ++c) G[c * HW + p] = h * f[c * HW + p];
+            }
+            for (int c = 0; c < d && rc == ORC_OK; ++c) {
+                rc = deriche_conv(G + c * HW, tmp, bar, H, W, &kc);
+#pragma omp parallel for schedule(static)
+                for (long long p = 0; p < (long long)HW; ++p) P[c * HW + p] += wt * conj(Hc[p]) * bar[p];
+            }
+            if (rc == ORC_OK) rc = deriche_conv(Hc, tmp, bar, H, W, &kc);
+#pragma omp parallel for schedule(static)
+            for (long long p = 0; p < (long long)HW; ++p) Zc[p] += wt * conj(Hc[p]) * bar[p];
+        }
+        if (rc == ORC_OK)
+            for (size_t p = 0; p < HW; ++p) {
+                for (int c = 0; c < d; ++c) {
+                    out[c * HW + p] = creal(P[c * HW + p]) / creal(Zc[p]);
+                    if (Pre) Pre[c * HW + p] = creal(P[c * HW + p]);
+                }
+                if (Zre) Zre[p] = creal(Zc[p]);
+            }
+    }
+    free(g); free(Hc); free(G); free(tmp); free(bar); free(P); free(Zc);
+    return rc;
+}
+
+/* Pairwise form of the same estimator with the recursive filter's 2-D kernel
+ * written out: weight h(|jx|) h(|jy|), h Deriche's closed form above, over
+ * every offset inside the image.  O(K H W) per pixel: tiny images only.  It
+ * checks the recursion coefficients against the closed form they come from. */
+int orc_mcsf_deriche_pairwise(int d, int H, int W, const double *f, double sigma_s, const double *Wm, int N, int K,
+                              const int32_t *Y, int npix, const int32_t *pix_yx, double *out) {
+    if (d < 1 || d > 8 || H < 1 || W < 1 || N < 1 || K < 1 || !(sigma_s > 0)) return ORC_ERR_ARG;
+    const size_t HW = (size_t)H * (size_t)W;
+    const double gamma = 1.0 / sqrt((double)N);
+    const int L = H > W ? H : W;
+    double *h = malloc(sizeof(double) * L);
+    if (!h) return ORC_ERR_NOMEM;
+    for (int n = 0; n < L; ++n) {
+        const double x = n / sigma_s;
+        h[n] = (DERICHE_FIT[0] * cos(DERICHE_FIT[3] * x) + DERICHE_FIT[1] * sin(DERICHE_FIT[3] * x)) *
+                   exp(-DERICHE_FIT[2] * x) +
+               (DERICHE_FIT[4] * cos(DERICHE_FIT[7] * x) + DERICHE_FIT[5] * sin(DERICHE_FIT[7] * x)) *
+                   exp(-DERICHE_FIT[6] * x);
+    }
+    for (int q = 0; q < npix; ++q) {
+        const int y = pix_yx[2 * q], x = pix_yx[2 * q + 1];
+        double num[8] = {0}, Z = 0.0;
+        for (int t = 0; t < K; ++t) {
+            double th_i = 0.0;
+            for (int k = 0; k < d; ++k) {
+                double gk = 0.0;
+                for (int c = 0; c < d; ++c) gk += Wm[k * d + c] * f[c * HW + (size_t)y * W + x];
+                th_i += Y[t * d + k] * gamma * gk;
+            }
+            for (int yy = 0; yy < H; ++yy)
+                for (int xx = 0; xx < W; ++xx) {
+                    double th_j = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        double gk = 0.0;
+                        for (int c = 0; c < d; ++c) gk += Wm[k * d + c] * f[c * HW + (size_t)yy * W + xx];
+                        th_j += Y[t * d + k] * gamma * gk;
+                    }
+                    const double w = h[abs(y - yy)] * h[abs(x - xx)] * cos(th_j - th_i) / K;
+                    Z += w;
+                    for (int c = 0; c < d; ++c) num[c] += w * f[c * HW + (size_t)yy * W + xx];
+                }
+        }
+        for (int c = 0; c < d; ++c) out[(size_t)q * d + c] = num[c] / Z;
+    }
+    free(h);
     return ORC_OK;
 }

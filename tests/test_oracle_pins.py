@@ -454,3 +454,74 @@ def test_lab_round_trip_and_continuity():
             hi = mid
     a, b = _lab_of([[lo - 1e-7] * 3, [lo + 1e-7] * 3])
     assert abs(a[0] - b[0]) < 1e-5
+
+
+# ------------------------------------------------------- recursive (Deriche) ---
+
+DERICHE_FIT = (1.680, 3.735, 1.783, 0.6318, -0.6803, -0.2598, 1.723, 1.997)  # Deriche 1993, Gaussian fit
+
+
+def _deriche_closed_form(n, s):
+    a0, a1, b0, w0, c0, c1, b1, w1 = DERICHE_FIT
+    t = np.abs(n) / s
+    return (a0 * np.cos(w0 * t) + a1 * np.sin(w0 * t)) * np.exp(-b0 * t) + \
+        (c0 * np.cos(w1 * t) + c1 * np.sin(w1 * t)) * np.exp(-b1 * t)
+
+
+@pytest.mark.parametrize("s", [1.5, 3.0, 8.0, 25.0])
+def test_deriche_recursion_equals_its_closed_form(s):
+    """Section 3 names Deriche's recursive Gaussian for the O(1) convolution.
+    The 4th-order causal + anticausal recursions (coefficients from the
+    z-transform of the two damped sinusoids) reproduce the closed-form kernel
+    h(|x|) h(|y|) of the fit exactly, and that kernel is within ~1e-3 of the
+    Gaussian it approximates (peak 1)."""
+    n = 301
+    x = np.zeros((n, n))
+    x[150, 150] = 1.0
+    h = O.deriche_blur(x, s)
+    m = np.arange(n) - 150
+    cf = _deriche_closed_form(m, s)
+    assert np.abs(h - np.outer(cf, cf)).max() < 1e-10
+    g = np.exp(-m ** 2 / (2 * s * s))
+    assert np.abs(h - np.outer(g, g)).max() < 1.5e-3
+
+
+def test_deriche_zero_state_is_zero_padding():
+    """Zero state at both ends of every line = zeros outside the image (R5)."""
+    rng = np.random.default_rng(3)
+    img = rng.uniform(0, 255, (23, 31))
+    pad = np.zeros((23 + 80, 31 + 80))
+    pad[40:63, 40:71] = img
+    a = O.deriche_blur(img, 4.0)
+    b = O.deriche_blur(pad, 4.0)[40:63, 40:71]
+    assert np.abs(a - b).max() < 1e-9 * np.abs(a).max()
+
+
+def test_mcsf_deriche_shiftable_equals_pairwise():
+    """Algorithm 1 with the recursive blur equals the pairwise sum with the
+    closed-form recursive kernel over the whole image (Eqs. bigExp-denom)."""
+    d, H, W, N, K, s = 3, 9, 11, 10, 4, 2.0
+    f = synth.voronoi_image(H, W, d, 4, 10.0, seed=5).astype(np.float64)
+    C = np.diag([40.0 ** 2] * d)
+    Wm = O.whiten(C, 0)
+    Y = O.sample_Y(d, N, K, 77)
+    S = O.mcsf_deriche(f, s, Wm, N, Y)["S"]
+    pix = np.array([(y, x) for y in range(H) for x in range(W)], np.int32)
+    pw = O.mcsf_deriche_pairwise(f, s, Wm, N, Y, pix)
+    assert np.allclose(pw.T.reshape(d, H, W), S, rtol=1e-9, atol=1e-9)
+
+
+def test_mcsf_deriche_infinite_range_and_constant_image():
+    """sigma_r -> inf: the recursive MCSF is the normalised recursive blur
+    (w * f) / (w * 1); a constant image is a fixed point."""
+    d, H, W, s = 3, 20, 17, 3.0
+    f = synth.voronoi_image(H, W, d, 5, 10.0, seed=8).astype(np.float64)
+    Wm = O.whiten(np.eye(d) * 1e16, 0)
+    Y = O.sample_Y(d, 10, 6, 3)
+    S = O.mcsf_deriche(f, s, Wm, 10, Y)["S"]
+    one = O.deriche_blur(np.ones((H, W)), s)
+    for c in range(d):
+        assert np.allclose(S[c], O.deriche_blur(f[c], s) / one, rtol=1e-9)
+    g = np.full((d, H, W), 77.0)
+    S = O.mcsf_deriche(g, s, O.whiten(np.eye(d) * 900.0, 0), 10, O.sample_Y(d, 10, 5, 4))["S"]
+    assert np.abs(S - 77.0).max() < 1e-9
