@@ -483,7 +483,8 @@ def run_sigma_sweep(args):
     cells plus noise of std 10) and on the 3840 x 2160 image of the headline
     workload.  Device time of one bf_filter per image (CUDA events, median of
     `--steps` launches after 3 warm-ups), for the tensor-core and the FP32
-    paths."""
+    windowed paths and the FP32 recursive (Deriche) path, whose cost does not
+    depend on sigma_s (the paper's Table 1 claim)."""
     import torch
     from paper_1605_02164_gb300 import bf
     from paper_1605_02164_gb300 import build as B
@@ -514,7 +515,7 @@ def run_sigma_sweep(args):
         for s in (1.0, 2.0, 3.0, 4.0, 5.0, 10.0):
             p = bf.bf_plan(3, C, s, 10, 300, args.seed + int(10 * s))
             row = {"H": H, "W": W, "sigma_s": s, "r": p.r}
-            for name in (args.variant, "fp32"):
+            for name in (args.variant, "fp32", "fp32rec"):
                 ms = median_ms(p, x, y, bf.VARIANTS[name])
                 row[f"{name}_ms"] = ms
                 row[f"{name}_mpx"] = H * W / ms / 1e3

@@ -54,7 +54,9 @@ extern "C" {
 #define BF_ERR_UNSUPPORTED (-9) /* parameters outside what the kernels handle */
 
 #define BF_MAX_D 8        /* channels per pixel */
-#define BF_MAX_RADIUS 32  /* window half-width r (sigma_s up to 10.99) */
+#define BF_MAX_RADIUS 32  /* window half-width r of the windowed variants (sigma_s up to 10.99) */
+#define BF_MAX_PLAN_RADIUS 4096 /* r of a plan (sigma_s up to 1365.6); beyond BF_MAX_RADIUS only
+                                   BF_FP32_RECURSIVE filters with it */
 #define BF_MAX_N 4096     /* raised-cosine order */
 #define BF_MAX_K 65536    /* Monte Carlo terms */
 
@@ -62,6 +64,9 @@ extern "C" {
 #define BF_FP32 0   /* every step in FP32 on the CUDA cores */
 #define BF_FP16TC 1 /* modulated channels in FP16, blur on tensor cores, FP32 accumulation */
 #define BF_BF16TC 2 /* as BF_FP16TC with BF16 channels */
+#define BF_FP32_RECURSIVE 3 /* FP32, the blur is Deriche's recursive Gaussian over the whole image
+                               (O(1) in sigma_s, Section 3): a different filter from the 3-sigma
+                               window (infinite support, ~1e-3 fit error); see bf_filter */
 
 /* Whitening of the range kernel (Eq. COB). */
 #define BF_WHITEN_CHOLESKY 0 /* W = L^{-1}, C = L L^T */
@@ -78,7 +83,8 @@ typedef struct bf_plan_s *bf_plan_t; /* opaque; owned by the library */
  *   C        host pointer, d*d doubles, row-major; symmetric positive definite
  *            (else BF_ERR_NOT_SPD; asymmetry beyond 1e-9 relative is BF_ERR_ARG).
  *   sigma_s  spatial standard deviation > 0; r = floor(3 sigma_s) must be
- *            <= BF_MAX_RADIUS (else BF_ERR_UNSUPPORTED).
+ *            <= BF_MAX_PLAN_RADIUS (else BF_ERR_UNSUPPORTED); the windowed
+ *            variants further need r <= BF_MAX_RADIUS at filter time.
  *   N        raised-cosine order, 1..BF_MAX_N; 0 selects 10, the order used
  *            in all of the paper's experiments.
  *   K        Monte Carlo terms (the paper's T), 1..BF_MAX_K.
@@ -119,8 +125,12 @@ int bf_plan_destroy(bf_plan_t plan);
  *            pixel; padding columns x >= W of out are not written.
  *   H, W     image size; H == 0 or W == 0 is a no-op returning BF_OK.
  *   pitch    row stride in elements, pitch >= W and pitch % 4 == 0.
- *   variant  BF_FP32, BF_FP16TC or BF_BF16TC.
+ *   variant  BF_FP32, BF_FP16TC, BF_BF16TC (windowed: r <= BF_MAX_RADIUS, else
+ *            BF_ERR_UNSUPPORTED; the tensor-core variants need d = 3) or
+ *            BF_FP32_RECURSIVE (any r; H <= 65535).
  * Pixels whose Re Z is exactly 0 come out as IEEE inf/nan; nothing is clamped.
+ * BF_FP32_RECURSIVE runs two kernels per term over the whole image and keeps
+ * 2 x 2(d+1) + (d+1) FP32 planes of scratch per call in library memory.
  */
 int bf_filter(bf_plan_t plan, const float *in, float *out, int H, int W, int pitch, int variant, void *stream);
 

@@ -30,6 +30,7 @@ BF_ERR_UNSUPPORTED = -9
 
 BF_MAX_D = 8
 BF_MAX_RADIUS = 32
+BF_MAX_PLAN_RADIUS = 4096
 BF_MAX_N = 4096
 BF_MAX_K = 65536
 BF_NOALLOC_MAX_ITEMS = 256
@@ -37,7 +38,8 @@ BF_NOALLOC_MAX_ITEMS = 256
 BF_FP32 = 0
 BF_FP16TC = 1
 BF_BF16TC = 2
-VARIANTS = {"fp32": BF_FP32, "fp16tc": BF_FP16TC, "bf16tc": BF_BF16TC}
+BF_FP32_RECURSIVE = 3
+VARIANTS = {"fp32": BF_FP32, "fp16tc": BF_FP16TC, "bf16tc": BF_BF16TC, "fp32rec": BF_FP32_RECURSIVE}
 
 BF_WHITEN_CHOLESKY = 0
 BF_WHITEN_EIGEN = 1

@@ -89,10 +89,12 @@ extern "C" int bf_filter(bf_plan_t p, const float *in, float *out, int H, int W,
     int rc = bf::check_image_args(p, in, out, H, W, pitch);
     if (rc != BF_OK || H == 0 || W == 0) return rc;
     cudaStream_t s = (cudaStream_t)stream;
+    if (variant != BF_FP32_RECURSIVE && p->r > BF_MAX_RADIUS) return BF_ERR_UNSUPPORTED;  // windowed kernels
     switch (variant) {
         case BF_FP32: return bf::launch_fp32(*p, in, out, H, W, pitch, s);
         case BF_FP16TC:
         case BF_BF16TC: return bf::launch_tc(*p, in, out, H, W, pitch, variant, s);
+        case BF_FP32_RECURSIVE: return bf::launch_recursive(*p, in, out, H, W, pitch, s);
         default: return BF_ERR_ARG;
     }
 }
@@ -103,6 +105,7 @@ extern "C" int bf_filter_batch(const bf_item *items, int n, int variant, void *s
         int rc = bf::check_image_args(items[i].plan, items[i].in, items[i].out, items[i].H, items[i].W,
                                       items[i].pitch);
         if (rc != BF_OK) return rc;
+        if (variant != BF_FP32_RECURSIVE && items[i].plan->r > BF_MAX_RADIUS) return BF_ERR_UNSUPPORTED;
     }
     cudaStream_t s = (cudaStream_t)stream;
     if (variant == BF_FP16TC || variant == BF_BF16TC) {
@@ -114,11 +117,12 @@ extern "C" int bf_filter_batch(const bf_item *items, int n, int variant, void *s
         if (!scratch || !st) return BF_ERR_NOMEM;
         return bf::tc_launch_batch(items, n, variant, scratch, st, s);
     }
-    if (variant != BF_FP32) return BF_ERR_ARG;
+    if (variant != BF_FP32 && variant != BF_FP32_RECURSIVE) return BF_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         const bf_item &it = items[i];
         if (it.H == 0 || it.W == 0) continue;
-        int rc = bf::launch_fp32(*it.plan, it.in, it.out, it.H, it.W, it.pitch, s);
+        int rc = variant == BF_FP32 ? bf::launch_fp32(*it.plan, it.in, it.out, it.H, it.W, it.pitch, s)
+                                    : bf::launch_recursive(*it.plan, it.in, it.out, it.H, it.W, it.pitch, s);
         if (rc != BF_OK) return rc;
     }
     return BF_OK;

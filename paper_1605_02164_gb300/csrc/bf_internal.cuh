@@ -43,6 +43,8 @@ int check_image_args(const bf_plan_s *p, const float *in, const float *out, int 
 
 // FP32 fused kernel (csrc/bf_fp32.cu).
 int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s);
+// Algorithm 1 with the recursive (Deriche) blur, FP32; scratch from stream_scratch.
+int launch_recursive(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s);
 
 // Tensor-core fused kernel (csrc/bf_tc.cu); variant BF_FP16TC or BF_BF16TC.
 int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int variant,

@@ -195,7 +195,7 @@ int make_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t see
         for (int j = 0; j < i; ++j)
             if (fabs(C[i * d + j] - C[j * d + i]) > 1e-9 * cmax) return BF_ERR_ARG;
     int r = radius >= 0 ? radius : (int)floor(3.0 * sigma_s + 1e-9);
-    if (r > BF_MAX_RADIUS) return BF_ERR_UNSUPPORTED;
+    if (r > BF_MAX_PLAN_RADIUS) return BF_ERR_UNSUPPORTED;
 
     bf_plan_s *p = new (std::nothrow) bf_plan_s;
     if (!p) return BF_ERR_NOMEM;

@@ -56,7 +56,7 @@ def test_host_side_argument_checks(lib):
     assert L.bf_plan(1, C, -1.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
     assert L.bf_plan(1, C, 2.0, 10, 0, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
     assert L.bf_plan(1, C, 2.0, 5000, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
-    assert L.bf_plan(1, C, 20.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_UNSUPPORTED
+    assert L.bf_plan(1, C, 1400.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_UNSUPPORTED
     asym = (ctypes.c_double * 4)(100.0, 1.0, 2.0, 100.0)
     assert L.bf_plan(2, asym, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
     assert L.bf_plan(1, None, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG
