@@ -262,7 +262,16 @@ def run_ours(args):
     peaks, peak_src = load_peaks()
     clocks = clk.summary()
     flops = algorithmic_flops_per_pixel(w.d, plan.r, w.K) * pixels
-    if variant == bf.BF_FP32:
+    if variant == bf.BF_FP32_RECURSIVE:
+        # whole-image multi-pass recursion: its traffic per pixel and term is
+        # rows 8d + 12 C2 (f twice, X written then read-modified-written) and
+        # columns 16 C2 + 4d + 8(d+1) (X twice, V out and back, f, P/Z), C2 = 2(d+1)
+        c2 = 2 * (w.d + 1)
+        design = (12 * w.d + 28 * c2 + 8 * (w.d + 1)) * pixels * w.K
+        roof = {"bound": "hbm", "achieved": design / (kernel_ms / 1e3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "peak_source": f"hbm_gbs ({peak_src})", "bytes_per_launch": design,
+                "bytes_kind": "design traffic of the two-pass recursion (FP32 X, V, P/Z planes in HBM)"}
+    elif variant == bf.BF_FP32:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
         roof = {"bound": "alu", "achieved": flops / (kernel_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -273,7 +282,8 @@ def run_ours(args):
                 "peak_source": f"bf16_tflops ({peak_src}); fp16 dense rate equals bf16"}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["traffic"] = args.traffic
-    roof["flops_per_launch"] = flops
+    if roof["bound"] != "hbm":
+        roof["flops_per_launch"] = flops
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -288,7 +298,7 @@ def run_ours(args):
                "sample": f"{size}x{size} central crop (+{plan.r}-px halo) of the {w.W}x{w.H} image, K={w.K}, "
                          f"FP64 Algorithm 1, {dt:.1f} s"}
 
-    dtype = {bf.BF_FP32: "f32", bf.BF_FP16TC: "f16", bf.BF_BF16TC: "bf16"}[variant]
+    dtype = {bf.BF_FP32: "f32", bf.BF_FP16TC: "f16", bf.BF_BF16TC: "bf16", bf.BF_FP32_RECURSIVE: "f32"}[variant]
     line = {
         "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -302,7 +312,7 @@ def run_ours(args):
         "fp32_value": fp32_mpx,
         "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": int(f.nbytes),
                 "d2h_bytes_per_step": int(f.nbytes), "api": "bf_filter_host (pinned host buffers)"},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 * math.ceil(w.K / 32) + 1 if variant == bf.BF_FP32_RECURSIVE else 1),
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
@@ -592,7 +602,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="fp16tc", choices=["fp32", "fp16tc", "bf16tc"])
+    ap.add_argument("--variant", default="fp16tc", choices=["fp32", "fp16tc", "bf16tc", "fp32rec"])
     ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS) + ["batch", "serve", "sigma-sweep", "lab"])
     ap.add_argument("--batch-n", type=int, default=64)
     ap.add_argument("--serve-seconds", type=float, default=0.25)

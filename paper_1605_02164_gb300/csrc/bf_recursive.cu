@@ -11,6 +11,8 @@
 // recursion: same filter, far better conditioned in FP32):
 //   causal      y_i(n) = q_i0 x(n) + q_i1 x(n-1) - p_i1 y_i(n-1) - p_i2 y_i(n-2)
 //   anticausal  v_i(n) = e_i1 x(n+1) + e_i2 x(n+2) - p_i1 v_i(n+1) - p_i2 v_i(n+2)
+// (each evaluated as the part that does not depend on the previous output,
+// then one FMA with it: one FMA per step on the recursion's critical path)
 // with p_i1 = -2 e^{-beta_i} cos om_i, p_i2 = e^{-2 beta_i}, q_i0 = a,
 // q_i1 = (c sin om_i - a cos om_i) e^{-beta_i}, e_i1 = q_i1 - q_i0 p_i1,
 // e_i2 = -q_i0 p_i2 (the z-transform of e^{-beta n}(a cos om n + c sin om n)
@@ -25,15 +27,16 @@
 //             thread per (row, channel) runs the causal sections left to right
 //             and writes X; then right to left the anticausal sections, adding
 //             into X.  Coalesced 128-byte row segments in and out.
-//   rec_cols  a block owns 16 columns; one thread per (column, channel) runs
-//             the anticausal sections bottom to top into V, then the causal
-//             ones top to bottom; each row's 2(d+1) blurred values meet in
-//             shared memory and are combined with the centre cos/sin into the
-//             P / Z accumulators (Eqs. numerator, denom, real parts).
-//             Loads run 8 rows ahead of the recursion.
-//   a final kernel divides P by Z.
-// Scratch (library-owned, per stream): X and V (2(d+1) planes each) and P/Z
-// (d + 1 planes), FP32, rows padded to 32.
+//   rec_cols  one thread per column carries all 2(d+1) channels: the
+//             anticausal sections bottom to top into V, then the causal ones
+//             top to bottom, each row's blurred values combined at once with
+//             the centre cos/sin into the P / Z accumulators (Eqs. numerator,
+//             denom, real parts).  No barriers; loads run 2-4 rows ahead.
+//   Up to 32 terms run per launch (grid.y), each with its own X, V and P / Z
+//   slot, so more independent recursions are in flight and the sum over
+//   terms has a fixed order; a final kernel adds the slots and divides.
+// Scratch (library-owned, per stream, at most 24 GB): per term slot X and V
+// (2(d+1) planes each) and P/Z (d + 1 planes), FP32, rows padded to 32.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -66,10 +69,10 @@ Sections make_sections(double sigma) {
     return S;
 }
 
-constexpr int kRowT = 256;  // rec_rows: 32 rows x 8 channel groups
-constexpr int kColT = 128;  // rec_cols: 16 columns x 8 channel groups
-constexpr int kCols = 16;
-constexpr int kAhead = 8;   // rows loaded ahead of the column recursion
+constexpr int kRowT = 256;       // rec_rows: 32 rows x 8 channel groups
+constexpr int kColT = 128;       // rec_cols: one column per thread
+constexpr int kTermBatch = 32;   // terms per launch (grid.y)
+constexpr size_t kScratchCap = (size_t)24 << 30;  // bound on the per-stream scratch of this variant
 
 // Phase of one pixel (turns), kept as in the FP32 kernel: FP32 product with its
 // exact residual and explicit reduction to [-1/2, 1/2], then sincospif.
@@ -91,11 +94,13 @@ __device__ __forceinline__ void centre_cs(const float *fv, const float *nh, cons
 template <int D>
 __global__ void __launch_bounds__(kRowT) rec_rows(const float *__restrict__ in, int pitch, int H, int W,
                                                   const float *__restrict__ nu_hi, const float *__restrict__ nu_lo,
-                                                  int k, float *__restrict__ X, int Wp, Sections S) {
+                                                  int k0, float *__restrict__ X, int Wp, size_t term_stride,
+                                                  Sections S) {
     constexpr int C2 = 2 * (D + 1);
     constexpr int CPT = (C2 + 7) / 8;  // channels per thread
     extern __shared__ float cb[];      // [C2][32][33]
-    const int tid = threadIdx.x, y0 = blockIdx.x * 32;
+    const int tid = threadIdx.x, y0 = blockIdx.x * 32, k = k0 + blockIdx.y;
+    X += blockIdx.y * term_stride;
     const size_t plane = (size_t)H * pitch, xplane = (size_t)H * Wp;
     float nh[D], nl[D];
 #pragma unroll
@@ -103,19 +108,24 @@ __global__ void __launch_bounds__(kRowT) rec_rows(const float *__restrict__ in, 
         nh[c] = __ldg(nu_hi + k * D + c);
         nl[c] = __ldg(nu_lo + k * D + c);
     }
+    // f of this thread's 4 pixels of a chunk, loaded one chunk ahead of build
+    float fpf[4][D];
+    auto load_f = [&](int cx) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int p = tid + kRowT * j, gy = y0 + (p >> 5), gx = cx + (p & 31);
+            const bool ok = gy < H && gx < W;
+#pragma unroll
+            for (int c = 0; c < D; ++c) fpf[j][c] = ok ? __ldg(in + c * plane + (size_t)gy * pitch + gx) : 0.f;
+        }
+    };
     auto build = [&](int cx) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = tid + kRowT * j, row = p >> 5, col = p & 31;
-            const int gy = y0 + row, gx = cx + col;
-            float fv[D], cs = 0.f, sn = 0.f;
-#pragma unroll
-            for (int c = 0; c < D; ++c) fv[c] = 0.f;
-            if (gy < H && gx < W) {
-#pragma unroll
-                for (int c = 0; c < D; ++c) fv[c] = __ldg(in + c * plane + (size_t)gy * pitch + gx);
-                centre_cs<D>(fv, nh, nl, cs, sn);
-            }
+            const float *fv = fpf[j];
+            float cs = 0.f, sn = 0.f;
+            if (y0 + row < H && cx + col < W) centre_cs<D>(fv, nh, nl, cs, sn);
             float *d = cb + row * 33 + col;
 #pragma unroll
             for (int c = 0; c < D; ++c) {
@@ -131,18 +141,21 @@ __global__ void __launch_bounds__(kRowT) rec_rows(const float *__restrict__ in, 
     float xs[CPT], a1[CPT], a2[CPT], b1[CPT], b2[CPT];
 #pragma unroll
     for (int u = 0; u < CPT; ++u) xs[u] = a1[u] = a2[u] = b1[u] = b2[u] = 0.f;
+    load_f(0);
     for (int cx = 0; cx < W; cx += 32) {
         build(cx);
+        if (cx + 32 < W) load_f(cx + 32);  // in flight during the recursion and the stores
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < CPT; ++u) {
             const int ch = g + 8 * u;
             if (ch < C2) {
                 float *line = cb + ch * 1056 + row * 33;
+#pragma unroll
                 for (int col = 0; col < 32; ++col) {
                     const float x = line[col];
-                    const float y0v = fmaf(S.q0[0], x, fmaf(S.q1[0], xs[u], fmaf(-S.p1[0], a1[u], -S.p2[0] * a2[u])));
-                    const float y1v = fmaf(S.q0[1], x, fmaf(S.q1[1], xs[u], fmaf(-S.p1[1], b1[u], -S.p2[1] * b2[u])));
+                    const float y0v = fmaf(-S.p1[0], a1[u], fmaf(S.q0[0], x, fmaf(S.q1[0], xs[u], -S.p2[0] * a2[u])));
+                    const float y1v = fmaf(-S.p1[1], b1[u], fmaf(S.q0[1], x, fmaf(S.q1[1], xs[u], -S.p2[1] * b2[u])));
                     xs[u] = x;
                     a2[u] = a1[u];
                     a1[u] = y0v;
@@ -165,18 +178,30 @@ __global__ void __launch_bounds__(kRowT) rec_rows(const float *__restrict__ in, 
     float x1[CPT], x2[CPT];
 #pragma unroll
     for (int u = 0; u < CPT; ++u) x1[u] = x2[u] = a1[u] = a2[u] = b1[u] = b2[u] = 0.f;
+    load_f(((W - 1) / 32) * 32);
     for (int cx = ((W - 1) / 32) * 32; cx >= 0; cx -= 32) {
         build(cx);
+        // the causal results this thread adds to, loaded before the recursion
+        float xr[C2][4];
+#pragma unroll
+        for (int ch = 0; ch < C2; ++ch)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int p = tid + kRowT * j, r = p >> 5, col = p & 31;
+                xr[ch][j] = (y0 + r < H && cx + col < W) ? X[ch * xplane + (size_t)(y0 + r) * Wp + cx + col] : 0.f;
+            }
+        if (cx >= 32) load_f(cx - 32);
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < CPT; ++u) {
             const int ch = g + 8 * u;
             if (ch < C2) {
                 float *line = cb + ch * 1056 + row * 33;
+#pragma unroll
                 for (int col = 31; col >= 0; --col) {
                     const float x = line[col];
-                    const float v0 = fmaf(S.e1[0], x1[u], fmaf(S.e2[0], x2[u], fmaf(-S.p1[0], a1[u], -S.p2[0] * a2[u])));
-                    const float v1 = fmaf(S.e1[1], x1[u], fmaf(S.e2[1], x2[u], fmaf(-S.p1[1], b1[u], -S.p2[1] * b2[u])));
+                    const float v0 = fmaf(-S.p1[0], a1[u], fmaf(S.e1[0], x1[u], fmaf(S.e2[0], x2[u], -S.p2[0] * a2[u])));
+                    const float v1 = fmaf(-S.p1[1], b1[u], fmaf(S.e1[1], x1[u], fmaf(S.e2[1], x2[u], -S.p2[1] * b2[u])));
                     x2[u] = x1[u];
                     x1[u] = x;
                     a2[u] = a1[u];
@@ -188,11 +213,13 @@ __global__ void __launch_bounds__(kRowT) rec_rows(const float *__restrict__ in, 
             }
         }
         __syncthreads();
+#pragma unroll
         for (int ch = 0; ch < C2; ++ch)
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int p = tid + kRowT * j, r = p >> 5, col = p & 31;
-                if (y0 + r < H && cx + col < W) X[ch * xplane + (size_t)(y0 + r) * Wp + cx + col] += cb[ch * 1056 + r * 33 + col];
+                if (y0 + r < H && cx + col < W)
+                    X[ch * xplane + (size_t)(y0 + r) * Wp + cx + col] = xr[ch][j] + cb[ch * 1056 + r * 33 + col];
             }
         __syncthreads();
     }
@@ -201,16 +228,18 @@ __global__ void __launch_bounds__(kRowT) rec_rows(const float *__restrict__ in, 
 template <int D>
 __global__ void __launch_bounds__(kColT) rec_cols(const float *__restrict__ in, int pitch, int H, int W,
                                                   const float *__restrict__ nu_hi, const float *__restrict__ nu_lo,
-                                                  int k, const float *__restrict__ X, float *__restrict__ V,
-                                                  float *__restrict__ PZ, int Wp, Sections S) {
+                                                  int k0, const float *__restrict__ X, float *__restrict__ V,
+                                                  float *__restrict__ PZ, int Wp, size_t term_stride, size_t pz_stride,
+                                                  Sections S) {
     constexpr int C2 = 2 * (D + 1);
-    constexpr int CPT = (C2 + 7) / 8;
-    constexpr int NPZ = (kCols * (D + 1) + kColT - 1) / kColT;  // P/Z values per thread per row
-    __shared__ float sB[C2][kCols];
-    __shared__ float2 sCS[kCols];
-    const int tid = threadIdx.x, col = tid & (kCols - 1), g = tid >> 4;
-    const int x = blockIdx.x * kCols + col;
-    const bool xin = x < W;
+    constexpr int AA = C2 <= 8 ? 4 : 2;  // rows loaded ahead of the anticausal recursion
+    constexpr int A = C2 <= 4 ? 4 : 2;   // and of the causal one (more live values)
+    const int x = blockIdx.x * kColT + threadIdx.x;
+    if (x >= W) return;  // no barriers in this kernel
+    const int j = blockIdx.y, k = k0 + j;
+    const float *Xj = X + j * term_stride;
+    float *Vj = V + j * term_stride;
+    float *PZj = PZ + j * pz_stride;
     const size_t plane = (size_t)H * pitch, xplane = (size_t)H * Wp;
     float nh[D], nl[D];
 #pragma unroll
@@ -219,123 +248,100 @@ __global__ void __launch_bounds__(kColT) rec_cols(const float *__restrict__ in, 
         nl[c] = __ldg(nu_lo + k * D + c);
     }
 
-    // anticausal, bottom to top, into V
-    float x1[CPT], x2[CPT], a1[CPT], a2[CPT], b1[CPT], b2[CPT];
+    // anticausal, bottom to top, into V: x(n+1), x(n+2), v_0(n+1), v_0(n+2), v_1(n+1), v_1(n+2)
+    float x1[C2], x2[C2], a1[C2], a2[C2], b1[C2], b2[C2];
 #pragma unroll
-    for (int u = 0; u < CPT; ++u) x1[u] = x2[u] = a1[u] = a2[u] = b1[u] = b2[u] = 0.f;
-    for (int yb = H - 1; yb >= 0; yb -= kAhead) {
-        float xv[CPT][kAhead];
+    for (int c = 0; c < C2; ++c) x1[c] = x2[c] = a1[c] = a2[c] = b1[c] = b2[c] = 0.f;
+    for (int yb = H - 1; yb >= 0; yb -= AA) {
+        float xv[AA][C2];
 #pragma unroll
-        for (int u = 0; u < CPT; ++u)
+        for (int a = 0; a < AA; ++a)
 #pragma unroll
-            for (int a = 0; a < kAhead; ++a) {
-                const int ch = g + 8 * u, y = yb - a;
-                xv[u][a] = (ch < C2 && xin && y >= 0) ? X[ch * xplane + (size_t)y * Wp + x] : 0.f;
-            }
+            for (int c = 0; c < C2; ++c) xv[a][c] = (yb - a >= 0) ? Xj[c * xplane + (size_t)(yb - a) * Wp + x] : 0.f;
 #pragma unroll
-        for (int a = 0; a < kAhead; ++a) {
+        for (int a = 0; a < AA; ++a) {
             const int y = yb - a;
             if (y < 0) break;
 #pragma unroll
-            for (int u = 0; u < CPT; ++u) {
-                const int ch = g + 8 * u;
-                const float v0 = fmaf(S.e1[0], x1[u], fmaf(S.e2[0], x2[u], fmaf(-S.p1[0], a1[u], -S.p2[0] * a2[u])));
-                const float v1 = fmaf(S.e1[1], x1[u], fmaf(S.e2[1], x2[u], fmaf(-S.p1[1], b1[u], -S.p2[1] * b2[u])));
-                x2[u] = x1[u];
-                x1[u] = xv[u][a];
-                a2[u] = a1[u];
-                a1[u] = v0;
-                b2[u] = b1[u];
-                b1[u] = v1;
-                if (ch < C2 && xin) V[ch * xplane + (size_t)y * Wp + x] = v0 + v1;
+            for (int c = 0; c < C2; ++c) {
+                const float v0 = fmaf(-S.p1[0], a1[c], fmaf(S.e1[0], x1[c], fmaf(S.e2[0], x2[c], -S.p2[0] * a2[c])));
+                const float v1 = fmaf(-S.p1[1], b1[c], fmaf(S.e1[1], x1[c], fmaf(S.e2[1], x2[c], -S.p2[1] * b2[c])));
+                x2[c] = x1[c];
+                x1[c] = xv[a][c];
+                a2[c] = a1[c];
+                a1[c] = v0;
+                b2[c] = b1[c];
+                b1[c] = v1;
+                Vj[c * xplane + (size_t)y * Wp + x] = v0 + v1;
             }
         }
     }
-    __syncthreads();  // V of this block's columns is complete (each thread reads only its own values back)
 
-    // causal, top to bottom, combined row by row into P / Z
-    float xp[CPT];
+    // causal, top to bottom, combined with the centre cos/sin into P / Z
 #pragma unroll
-    for (int u = 0; u < CPT; ++u) xp[u] = a1[u] = a2[u] = b1[u] = b2[u] = 0.f;
-    for (int yb = 0; yb < H; yb += kAhead) {
-        float xv[CPT][kAhead], vv[CPT][kAhead];
+    for (int c = 0; c < C2; ++c) x1[c] = a1[c] = a2[c] = b1[c] = b2[c] = 0.f;  // x1 = x(n-1) here
+    for (int yb = 0; yb < H; yb += A) {
+        float xv[A][C2], vv[A][C2], fv[A][D], pz[A][D + 1];
 #pragma unroll
-        for (int u = 0; u < CPT; ++u)
+        for (int a = 0; a < A; ++a) {
+            const bool ok = yb + a < H;
+            const size_t o = (size_t)(yb + a) * Wp + x;
 #pragma unroll
-            for (int a = 0; a < kAhead; ++a) {
-                const int ch = g + 8 * u, y = yb + a;
-                const bool ok = ch < C2 && xin && y < H;
-                xv[u][a] = ok ? X[ch * xplane + (size_t)y * Wp + x] : 0.f;
-                vv[u][a] = ok ? V[ch * xplane + (size_t)y * Wp + x] : 0.f;
+            for (int c = 0; c < C2; ++c) {
+                xv[a][c] = ok ? Xj[c * xplane + o] : 0.f;
+                vv[a][c] = ok ? Vj[c * xplane + o] : 0.f;
             }
-        // centre values (group 0) and the P / Z accumulators of these rows
-        float fc[kAhead][D];
-        if (g == 0) {
 #pragma unroll
-            for (int a = 0; a < kAhead; ++a)
+            for (int c = 0; c <= D; ++c) pz[a][c] = ok ? PZj[c * xplane + o] : 0.f;
 #pragma unroll
-                for (int c = 0; c < D; ++c)
-                    fc[a][c] = (xin && yb + a < H) ? __ldg(in + c * plane + (size_t)(yb + a) * pitch + x) : 0.f;
-        }
-        float acc[NPZ][kAhead];
-#pragma unroll
-        for (int i = 0; i < NPZ; ++i) {
-            const int t = tid + kColT * i, cc = t >> 4, xx = blockIdx.x * kCols + (t & (kCols - 1));
-#pragma unroll
-            for (int a = 0; a < kAhead; ++a)
-                acc[i][a] = (cc <= D && xx < W && yb + a < H) ? PZ[cc * xplane + (size_t)(yb + a) * Wp + xx] : 0.f;
+            for (int c = 0; c < D; ++c) fv[a][c] = ok ? __ldg(in + c * plane + (size_t)(yb + a) * pitch + x) : 0.f;
         }
 #pragma unroll
-        for (int a = 0; a < kAhead; ++a) {
-            const int y = yb + a;
-            if (y >= H) break;
+        for (int a = 0; a < A; ++a) {
+            if (yb + a >= H) break;
+            float B[C2];
 #pragma unroll
-            for (int u = 0; u < CPT; ++u) {
-                const int ch = g + 8 * u;
-                const float xn = xv[u][a];
-                const float y0v = fmaf(S.q0[0], xn, fmaf(S.q1[0], xp[u], fmaf(-S.p1[0], a1[u], -S.p2[0] * a2[u])));
-                const float y1v = fmaf(S.q0[1], xn, fmaf(S.q1[1], xp[u], fmaf(-S.p1[1], b1[u], -S.p2[1] * b2[u])));
-                xp[u] = xn;
-                a2[u] = a1[u];
-                a1[u] = y0v;
-                b2[u] = b1[u];
-                b1[u] = y1v;
-                if (ch < C2) sB[ch][col] = y0v + y1v + vv[u][a];
+            for (int c = 0; c < C2; ++c) {
+                const float xn = xv[a][c];
+                const float y0v = fmaf(-S.p1[0], a1[c], fmaf(S.q0[0], xn, fmaf(S.q1[0], x1[c], -S.p2[0] * a2[c])));
+                const float y1v = fmaf(-S.p1[1], b1[c], fmaf(S.q0[1], xn, fmaf(S.q1[1], x1[c], -S.p2[1] * b2[c])));
+                x1[c] = xn;
+                a2[c] = a1[c];
+                a1[c] = y0v;
+                b2[c] = b1[c];
+                b1[c] = y1v;
+                B[c] = y0v + y1v + vv[a][c];
             }
-            if (g == 0) {
-                float c_, s_;
-                centre_cs<D>(fc[a], nh, nl, c_, s_);
-                sCS[col] = make_float2(c_, s_);
-            }
-            __syncthreads();
+            float cs, sn;
+            centre_cs<D>(fv[a], nh, nl, cs, sn);
 #pragma unroll
-            for (int i = 0; i < NPZ; ++i) {
-                const int t = tid + kColT * i, cc = t >> 4, cl = t & (kCols - 1);
-                if (cc <= D) {
-                    const float2 cs = sCS[cl];
-                    acc[i][a] = fmaf(cs.x, sB[cc][cl], fmaf(cs.y, sB[D + 1 + cc][cl], acc[i][a]));
-                }
-            }
-            __syncthreads();
+            for (int c = 0; c <= D; ++c) pz[a][c] = fmaf(cs, B[c], fmaf(sn, B[D + 1 + c], pz[a][c]));
         }
 #pragma unroll
-        for (int i = 0; i < NPZ; ++i) {
-            const int t = tid + kColT * i, cc = t >> 4, xx = blockIdx.x * kCols + (t & (kCols - 1));
+        for (int a = 0; a < A; ++a)
+            if (yb + a < H) {
+                const size_t o = (size_t)(yb + a) * Wp + x;
 #pragma unroll
-            for (int a = 0; a < kAhead; ++a)
-                if (cc <= D && xx < W && yb + a < H) PZ[cc * xplane + (size_t)(yb + a) * Wp + xx] = acc[i][a];
-        }
+                for (int c = 0; c <= D; ++c) PZj[c * xplane + o] = pz[a][c];
+            }
     }
 }
 
+// out_c = sum_j P_j,c / sum_j Z_j over the term slots.
 template <int D>
-__global__ void rec_divide(const float *__restrict__ PZ, int Wp, float *__restrict__ out, int pitch, int H, int W) {
+__global__ void rec_divide(const float *__restrict__ PZ, int Wp, size_t pz_stride, int slots, float *__restrict__ out,
+                           int pitch, int H, int W) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= W) return;
-    const size_t xplane = (size_t)H * Wp, plane = (size_t)H * pitch;
-    const float z = PZ[D * xplane + (size_t)y * Wp + x];
+    const size_t xplane = (size_t)H * Wp, plane = (size_t)H * pitch, o = (size_t)y * Wp + x;
+    float acc[D + 1];
 #pragma unroll
-    for (int c = 0; c < D; ++c) out[c * plane + (size_t)y * pitch + x] = PZ[c * xplane + (size_t)y * Wp + x] / z;
+    for (int c = 0; c <= D; ++c) acc[c] = 0.f;
+    for (int j = 0; j < slots; ++j)
+#pragma unroll
+        for (int c = 0; c <= D; ++c) acc[c] += PZ[j * pz_stride + c * xplane + o];
+#pragma unroll
+    for (int c = 0; c < D; ++c) out[c * plane + (size_t)y * pitch + x] = acc[c] / acc[D];
 }
 
 template <int D>
@@ -343,11 +349,17 @@ int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int 
     constexpr int C2 = 2 * (D + 1);
     const int Wp = (W + 31) / 32 * 32;
     const size_t xplane = (size_t)H * Wp;
-    const size_t bytes = (2 * C2 + (D + 1)) * xplane * sizeof(float);
-    float *X = (float *)bf::stream_scratch(s, bytes);
+    const size_t term_stride = C2 * xplane, pz_stride = (D + 1) * xplane;
+    // Terms run kTermBatch at a time (grid.y), each with its own X, V and P/Z
+    // slot: more independent recursions in flight, and a fixed summation order.
+    const size_t per_term = (2 * term_stride + pz_stride) * sizeof(float);
+    int tb = kTermBatch;
+    if (tb > p.K) tb = p.K;
+    while (tb > 1 && (size_t)tb * per_term > kScratchCap) --tb;
+    float *X = (float *)bf::stream_scratch(s, (size_t)tb * per_term);
     if (!X) return BF_ERR_NOMEM;
-    float *V = X + C2 * xplane, *PZ = V + C2 * xplane;
-    int rc = bf::cuda_err(cudaMemsetAsync(PZ, 0, (D + 1) * xplane * sizeof(float), s));
+    float *V = X + (size_t)tb * term_stride, *PZ = V + (size_t)tb * term_stride;
+    int rc = bf::cuda_err(cudaMemsetAsync(PZ, 0, (size_t)tb * pz_stride * sizeof(float), s));
     if (rc != BF_OK) return rc;
     const Sections S = make_sections(p.sigma_s);
     const int smem = C2 * 32 * 33 * (int)sizeof(float);
@@ -355,12 +367,16 @@ int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int 
         rc = bf::cuda_err(cudaFuncSetAttribute(rec_rows<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         if (rc != BF_OK) return rc;
     }
-    const unsigned row_blocks = (unsigned)((H + 31) / 32), col_blocks = (unsigned)((W + kCols - 1) / kCols);
-    for (int k = 0; k < p.K; ++k) {
-        rec_rows<D><<<row_blocks, kRowT, smem, s>>>(in, pitch, H, W, p.nu_hi, p.nu_lo, k, X, Wp, S);
-        rec_cols<D><<<col_blocks, kColT, 0, s>>>(in, pitch, H, W, p.nu_hi, p.nu_lo, k, X, V, PZ, Wp, S);
+    const unsigned row_blocks = (unsigned)((H + 31) / 32), col_blocks = (unsigned)((W + kColT - 1) / kColT);
+    for (int k0 = 0; k0 < p.K; k0 += tb) {
+        const unsigned nb = (unsigned)(p.K - k0 < tb ? p.K - k0 : tb);
+        rec_rows<D><<<dim3(row_blocks, nb), kRowT, smem, s>>>(in, pitch, H, W, p.nu_hi, p.nu_lo, k0, X, Wp,
+                                                              term_stride, S);
+        rec_cols<D><<<dim3(col_blocks, nb), kColT, 0, s>>>(in, pitch, H, W, p.nu_hi, p.nu_lo, k0, X, V, PZ, Wp,
+                                                           term_stride, pz_stride, S);
     }
-    rec_divide<D><<<dim3((unsigned)((W + 127) / 128), (unsigned)H), 128, 0, s>>>(PZ, Wp, out, pitch, H, W);
+    rec_divide<D><<<dim3((unsigned)((W + 127) / 128), (unsigned)H), 128, 0, s>>>(PZ, Wp, pz_stride, tb, out, pitch,
+                                                                                 H, W);
     return bf::cuda_err(cudaGetLastError());
 }
 

@@ -6,9 +6,10 @@ Tolerance, derived from the arithmetic: the FP32 recursions leave an absolute
 error of ~3e-4 x (kernel weight Sum w) on the 0..255 scale in P and Z (a
 float32 emulation of the same two-section recursion reproduces the GPU's
 errors; in float64 it matches the oracle to 5e-9), and S = P / Z scales it by
-Sum w / Re Z.  So: max-abs <= 1e-3 where Re Z >= 0.1 Sum w, and
-|error| <= 1e-3 Sum w / Re Z elsewhere; pixels with Re Z < 1e-2 Sum w (near-zero
-normaliser) are excluded and counted, as for the windowed paths."""
+Sum w / Re Z (measured: |error| Re Z / Sum w <= 2.7e-4).  So:
+|error| <= 1e-3 max(1, 0.5 Sum w / Re Z), i.e. max-abs <= 1e-3 where
+Re Z >= 0.5 Sum w; pixels with Re Z < 1e-2 Sum w (near-zero normaliser) are
+excluded and counted, as for the windowed paths."""
 import numpy as np
 import pytest
 
@@ -47,14 +48,13 @@ def _check(bf, f, C, s, N, K, seed, tol=1e-3):
     one = O.deriche_blur(np.ones((H, W)), s)  # total kernel weight per pixel (Z with all phases equal)
     zr = res["Zre"] / one
     mask = zr >= 1e-2
-    bulk = zr >= 0.1
     err = np.abs(got - res["S"])
-    print(f"recursive d={d} {H}x{W} s={s} K={K}: max-abs {err[:, bulk].max():.3e} (Re Z >= 0.1 Sum w), "
+    bound = tol * np.maximum(1.0, 0.5 / np.maximum(zr, 1e-2))
+    print(f"recursive d={d} {H}x{W} s={s} K={K}: max-abs {err[:, zr >= 0.5].max():.3e} (Re Z >= 0.5 Sum w), "
           f"max err x Re Z / Sum w {(err * zr)[:, mask].max():.3e}, low-Z {(~mask).sum()}")
     assert (~mask).mean() <= 0.005
     assert np.isfinite(got[:, mask]).all()
-    assert err[:, bulk].max() <= tol
-    assert (err[:, mask] <= tol / zr[mask]).all()
+    assert (err[:, mask] <= bound[mask]).all()
     assert bf.bf_last_status(0) == bf.BF_OK
     return got
 
