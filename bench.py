@@ -643,8 +643,8 @@ def run_lab(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--variant", default="fp16tc", choices=["fp32", "fp16tc", "bf16tc", "fp32rec"])
     ap.add_argument("--workload", default="4k", choices=sorted(synth.WORKLOADS) + ["batch", "serve", "sigma-sweep", "lab"])
