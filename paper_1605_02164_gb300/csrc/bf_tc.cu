@@ -7,17 +7,18 @@
 // plus an r-pixel halo, at most 128 x 128 pixels) stays resident in tensor
 // memory as FP32 for all K terms.  For each term the region is streamed in
 // chunks of 16 rows:
-//   A  (all threads) phase theta = 2 pi nu.f in FP32 with range reduction,
-//      cos/sin, and the 8 modulated channels cos f_c, cos, sin f_c, sin of
-//      16 rows x 128 columns, stored as FP16/BF16 in the K-major operand
-//      layout (M = 16 rows x 8 channels = 128, K = columns);
-//   M1 (one thread) horizontal pass: 4 output-column blocks of 16, each
-//      D1[128 x 16] = A1[128 x Kw] * T[Kw x 16], T the Toeplitz band of the
-//      normalised 1-D taps (Kw = 16 + 16 ceil(2r/16));
+//   A  (all threads) phase theta = 2 pi nu.f in FP32 radians, SFU cos/sin,
+//      and the 8 modulated channels cos f_c, cos, sin f_c, sin of 16 rows x
+//      128 columns, stored as FP16/BF16 in the K-major operand layout
+//      (M = 16 rows x 8 channels = 128, K = columns);
+//   M1 (one thread) horizontal pass, one chain of m128n64k16 MMAs:
+//      D1[128 x 64] = A1[128 x Kw1] * T1[Kw1 x 64], T1 the Toeplitz band of
+//      the normalised 1-D taps (Kw1 = 16 ceil((64 + 2r) / 16));
 //   X  (all threads) D1 (TMEM) -> FP16/BF16 into a ring of horizontally
 //      blurred rows, laid out MN-major (M = 64 columns x 8 channels);
-//   M2 (one thread) vertical pass for the 16 output rows that became
-//      complete: 4 M-tiles D2[128 x 16] = A2[128 x Kw] * T[Kw x 16];
+//   M2 (4 threads) vertical pass for the 16 output rows that became
+//      complete: 4 M-tiles D2[128 x 16] = A2[128 x Kw] * T2[Kw x 16]
+//      (Kw = 16 + 16 ceil(2r / 16));
 //   C  (all threads) combine with the centre pixel's cos/sin into
 //      register accumulators P_1..P_3, Z (FP32).
 // After the last term out_c = P_c / Z.  Every wait on the tensor core is
@@ -200,7 +201,7 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // Persistent kernel: each CTA keeps its tensor memory and pops tiles (of all
 // images) from a device work counter until the queue is empty.
 // Per tile, a software pipeline over the flat sequence of (term, 16-row chunk)
-// steps s = k * nc + c.  All 8 warps in step s
+// steps s = k * nc + c.  All 16 warps in step s
 //   1  build the channels of chunk s+1 (A) into the A1 buffer not being read,
 //   1b wait for the vertical MMAs issued in step s-1 and combine them (C),
 //   2  wait for the horizontal MMAs of chunk s and move D1 into the ring (X),
