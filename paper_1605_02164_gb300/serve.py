@@ -7,11 +7,14 @@ time.  The server
     an LRU cache keyed by (d, C, sigma_s, N, K, seed, whitening);
   * admits queued requests in arrival order while the device memory they need
     (their output buffer; inputs are the caller's) fits in the budget, and
-    rejects a request larger than the whole budget;
-  * launches whatever has been admitted as one bf_filter_batch call on the
-    next free stream as soon as one is free, so requests that arrive while
-    others are on the GPU join the next batch and their work overlaps the
-    batches already running (continuous batching);
+    rejects a request larger than the whole budget (BF_ERR_BUDGET) or one whose
+    window the windowed kernels cannot hold (r > BF_MAX_RADIUS: BF_ERR_UNSUPPORTED
+    unless the request asks for the recursive variant);
+  * launches whatever has been admitted as one bf_filter_batch call per kernel
+    variant on the next free stream as soon as one is free (RGB on the tensor
+    cores, other d on the FP32 kernel, or the variant a request names), so
+    requests that arrive while others are on the GPU join the next batch and
+    their work overlaps the batches already running (continuous batching);
   * completes requests as their batch's event fires, frees their budget and
     records per-request latency (arrival to completion).
 Every filtering step runs in libbf's kernels; this module only schedules.
@@ -43,6 +46,7 @@ class Request:
     N: int = 10
     seed: int = 0
     whiten: int = bf.BF_WHITEN_CHOLESKY
+    variant: int | None = None  # None: the server's choice; else a BF_* variant for this request
     t_arrival: float = 0.0
     rid: int = 0
     out: object = None
@@ -99,9 +103,15 @@ class Server:
             req.t_arrival = time.perf_counter()
         d, H, W = req.x.shape
         req._bytes = d * H * req.x.stride(1) * 4
+        r = int(math.floor(3.0 * req.sigma_s + 1e-9))
         with self.cv:
+            reason = None
             if req._bytes > self.budget:
-                req.status = bf.BF_ERR_BUDGET
+                reason = bf.BF_ERR_BUDGET
+            elif r > bf.BF_MAX_RADIUS and req.variant != bf.BF_FP32_RECURSIVE:
+                reason = bf.BF_ERR_UNSUPPORTED  # the windowed kernels hold r <= BF_MAX_RADIUS
+            if reason is not None:
+                req.status = reason
                 req.t_done = time.perf_counter()
                 self.rejected.append(req)
                 req.done_evt.set()
@@ -147,11 +157,18 @@ class Server:
                 batch.append(r)
         return batch
 
+    def _variant_of(self, r: Request, d: int) -> int:
+        if r.variant is not None:
+            return r.variant
+        if self.variant in (bf.BF_FP16TC, bf.BF_BF16TC) and d != 3:
+            return bf.BF_FP32  # the tensor-core kernel is for RGB
+        return self.variant
+
     def _launch(self, i: int, batch: list[Request]):
         torch = self.torch
         s = self.streams[i]
         now = time.perf_counter()
-        tc, fp = [], []
+        groups: dict[int, list] = {}
         with torch.cuda.stream(s):
             for r in batch:
                 r.t_admit = now
@@ -159,15 +176,13 @@ class Server:
                 r.out = torch.empty_strided(r.x.shape, r.x.stride(), dtype=torch.float32, device=self.dev)
                 p = self.plan(d, r.C, r.sigma_s, r.N, r.K, r.seed, r.whiten)
                 item = (p, r.x.data_ptr(), r.out.data_ptr(), H, W, r.x.stride(1))
-                (tc if (self.variant != bf.BF_FP32 and d == 3) else fp).append(item)
-            try:
-                if tc:
-                    bf.bf_filter_batch(tc, self.variant, s.cuda_stream)
-                if fp:
-                    bf.bf_filter_batch(fp, bf.BF_FP32, s.cuda_stream)
-            except bf.BFError as e:
-                for r in batch:
-                    r.status = e.code
+                groups.setdefault(self._variant_of(r, d), []).append((item, r))
+            for v, members in groups.items():
+                try:
+                    bf.bf_filter_batch([it for it, _ in members], v, s.cuda_stream)
+                except bf.BFError as e:
+                    for _, r in members:
+                        r.status = e.code
             evt = torch.cuda.Event()
             evt.record(s)
         self.busy[i] = (evt, batch)

@@ -92,3 +92,29 @@ def test_budget_admission_and_rejection(bf):
     s = summarize(reqs, t0, time.perf_counter())
     assert s["completed"] == len(reqs) and s["failed"] == 0
     assert srv.used == 0
+
+
+def test_wide_window_rejected_alone_and_recursive_request_served(bf):
+    """A request whose window exceeds the windowed kernels (sigma_s = 12, r = 36)
+    is rejected by itself with BF_ERR_UNSUPPORTED; the same request asking for
+    the recursive variant is served and equals a lone call; the rest of the
+    batch completes."""
+    from paper_1605_02164_gb300.serve import Request, Server
+    reqs = _requests(bf, 4, seed=11)
+    f = synth.voronoi_image(90, 70, 3, 6, 10.0, seed=3)
+    C = np.diag([40.0 ** 2] * 3)
+    wide = Request(bf.to_pitched(f), C, 12.0, 16, 10, seed=5, rid=50)
+    wide_rec = Request(bf.to_pitched(f), C, 12.0, 16, 10, seed=5, rid=51, variant=bf.BF_FP32_RECURSIVE)
+    srv = Server(budget_bytes=64 << 20, streams=2, max_batch=8).start()
+    for r in reqs + [wide, wide_rec]:
+        srv.submit(r)
+    assert wide.status == bf.BF_ERR_UNSUPPORTED and wide.done_evt.is_set()
+    for r in reqs + [wide_rec]:
+        assert r.done_evt.wait(120)
+    srv.close()
+    assert all(r.status == 0 for r in reqs) and wide_rec.status == 0
+    p = bf.bf_plan(3, C, 12.0, 10, 16, 5)
+    alone = bf.filter_tensor(p, wide_rec.x, bf.BF_FP32_RECURSIVE)
+    torch.cuda.synchronize()
+    assert torch.equal(alone, wide_rec.out)
+    assert srv.used == 0
