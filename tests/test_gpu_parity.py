@@ -122,6 +122,7 @@ def test_fp32_small_config_full_image(bf):
     (6, 60, 50, 2.0, 10, 8, 14),     # 6 channels, one pass per term
     (6, 50, 70, 8.0, 10, 24, 12),    # 6 channels, r = 24: cos and sin groups in two passes
     (8, 40, 45, 10.5, 10, 24, 13),   # 8 channels, r = 31: two passes
+    (3, 70, 96, 10.9, 10, 6, 15),    # r = 32 = BF_MAX_RADIUS
 ])
 def test_fp32_ragged_and_edge_shapes(bf, d, H, W, s, N, K, seed):
     if d == 1:
@@ -291,6 +292,8 @@ def test_tc_small_config_full_image(bf, variant):
     (70, 90, 10.5, 10, 4, 10),     # r = 31
     (20, 33, 0.2, 10, 4, 9),       # r = 0
     (300, 260, 5.0, 12, 12, 11),   # r = 15, several row tiles
+    (80, 130, 10.9, 10, 6, 15),    # r = 32 = BF_MAX_RADIUS
+    (160, 128, 8.0, 10, 8, 16),    # width a multiple of the 64-column tile, height of the 80-row tile
 ])
 def test_tc_ragged_and_edge_shapes(bf, H, W, s, N, K, seed):
     d = 3
