@@ -292,8 +292,8 @@ def test_tc_small_config_full_image(bf, variant):
     (70, 90, 10.5, 10, 4, 10),     # r = 31
     (20, 33, 0.2, 10, 4, 9),       # r = 0
     (300, 260, 5.0, 12, 12, 11),   # r = 15, several row tiles
-    (80, 130, 10.9, 10, 6, 15),    # r = 32 = BF_MAX_RADIUS
-    (160, 128, 8.0, 10, 8, 16),    # width a multiple of the 64-column tile, height of the 80-row tile
+    (80, 130, 10.9, 10, 32, 15),   # r = 32 = BF_MAX_RADIUS
+    (160, 128, 8.0, 10, 32, 16),   # width a multiple of the 64-column tile, height of the 80-row tile
 ])
 def test_tc_ragged_and_edge_shapes(bf, H, W, s, N, K, seed):
     d = 3
