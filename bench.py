@@ -164,12 +164,13 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_oracle_step(f, w, ref, y0, x0, size):
-    """Oracle part B (Algorithm 1, FP64) on a size x size crop plus its halo."""
+def cpu_oracle_step(f, w, ref, y0, x0, size, size_x=None):
+    """Oracle part B (Algorithm 1, FP64) on a size x size_x crop plus its halo."""
     import oracle as O
     r = ref["r"]
+    size_x = size if size_x is None else size_x
     ya, yb = max(0, y0 - r), min(w.H, y0 + size + r)
-    xa, xb = max(0, x0 - r), min(w.W, x0 + size + r)
+    xa, xb = max(0, x0 - r), min(w.W, x0 + size_x + r)
     reg = f[:, ya:yb, xa:xb].astype(np.float64)
     O.mcsf(reg, w.sigma_s, ref["W"], w.N, ref["Y"])
 
@@ -183,25 +184,25 @@ def run_reference(args):
     w = synth.WORKLOADS[args.workload]()
     f = w.image()
     ref = O.plan(w.d, w.C, w.sigma_s, w.N, w.K, args.seed)
-    size = args.ref_crop
-    y0, x0 = (w.H - size) // 2, (w.W - size) // 2
+    sh, sw = min(args.ref_crop, w.H), min(args.ref_crop, w.W)
+    y0, x0 = (w.H - sh) // 2, (w.W - sw) // 2
     for _ in range(args.warmup):
-        cpu_oracle_step(f, w, ref, y0, x0, size)
+        cpu_oracle_step(f, w, ref, y0, x0, sh, sw)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        cpu_oracle_step(f, w, ref, y0, x0, size)
+        cpu_oracle_step(f, w, ref, y0, x0, sh, sw)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
-    mpx = args.steps * size * size / tot / 1e6
+    mpx = args.steps * sh * sw / tot / 1e6
     cores = O.num_threads()
-    sample = f"{size}x{size} central crop (+{ref['r']}-px halo) of the {w.W}x{w.H} image, K={w.K}, per step"
+    sample = f"{sw}x{sh} central crop (+{ref['r']}-px halo) of the {w.W}x{w.H} image, K={w.K}, per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": mpx, "unit": "Mpixel/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": w.name, "H": w.H, "W": w.W, "d": w.d,
-                                        "sigma_s": w.sigma_s, "N": w.N, "K": w.K, "crop": size},
+                                        "sigma_s": w.sigma_s, "N": w.N, "K": w.K, "crop": [sw, sh]},
         "cpu_baseline": {"value": mpx, "unit": "Mpixel/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": mpx, "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "latency_ms": {"p50": 1e3 * float(np.percentile(times, 50)), "p99": 1e3 * float(np.percentile(times, 99))},
@@ -332,14 +333,20 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         import oracle as O
         ref = O.plan(w.d, w.C, w.sigma_s, w.N, w.K, args.seed)
-        size = args.cpu_crop
-        y0, x0 = (w.H - size) // 2, (w.W - size) // 2
+        sh, sw = min(args.cpu_crop, w.H), min(args.cpu_crop, w.W)
+        y0, x0 = (w.H - sh) // 2, (w.W - sw) // 2
         t0 = time.perf_counter()
-        cpu_oracle_step(f, w, ref, y0, x0, size)
+        cpu_oracle_step(f, w, ref, y0, x0, sh, sw)
         dt = time.perf_counter() - t0
-        cpu = {"value": size * size / dt / 1e6, "unit": "Mpixel/s", "cores": O.num_threads(), "kind": "oracle",
-               "sample": f"{size}x{size} central crop (+{plan.r}-px halo) of the {w.W}x{w.H} image, K={w.K}, "
+        cpu = {"value": sh * sw / dt / 1e6, "unit": "Mpixel/s", "cores": O.num_threads(), "kind": "oracle",
+               "sample": f"{sw}x{sh} central crop (+{plan.r}-px halo) of the {w.W}x{w.H} image, K={w.K}, "
                          f"FP64 Algorithm 1, {dt:.1f} s"}
+        if w.H * w.W <= 512 * 512:  # the direct filter (part A) too, on small images
+            t0 = time.perf_counter()
+            O.direct(f.astype(np.float64), w.sigma_s, w.C)
+            dt = time.perf_counter() - t0
+            cpu["direct_value"] = w.H * w.W / dt / 1e6
+            cpu["direct_sample"] = f"whole {w.W}x{w.H} image, FP64 direct filter (Eqs. BF, normal), {dt:.2f} s"
 
     dtype = {bf.BF_FP32: "f32", bf.BF_FP16TC: "f16", bf.BF_BF16TC: "bf16", bf.BF_FP32_RECURSIVE: "f32"}[variant]
     line = {
