@@ -144,10 +144,14 @@ typedef struct {
 
 /*
  * bf_filter_batch -- filter n independent images (each with its own plan,
- * size, d, sigma_s and K) in one persistent-kernel launch that pops tiles of
- * all images from a device work queue.  Same rules per item as bf_filter.
- * Results equal those of n separate bf_filter calls with the same variant.
- * `items` is a host array; it is copied before the call returns.
+ * size, d, sigma_s and K).  Tensor-core variants: one persistent-kernel launch
+ * that pops tiles of all images from a device work queue.  BF_FP32: one
+ * launch per image, spread over 4 library-owned streams that are ordered
+ * after the work already on `stream` and before anything queued on it later
+ * (images run concurrently).  BF_FP32_RECURSIVE: one image after another on
+ * `stream`.  Same rules per item as bf_filter; results equal those of n
+ * separate bf_filter calls with the same variant.  `items` is a host array;
+ * it is read before the call returns.
  */
 int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
 

@@ -99,6 +99,62 @@ extern "C" int bf_filter(bf_plan_t p, const float *in, float *out, int H, int W,
     }
 }
 
+namespace {
+// Library-owned streams for the per-image FP32 launches of a batch.  A small
+// image fills few of the SMs, so the images of a batch run concurrently on
+// these streams; events order them after the work already queued on the
+// caller's stream and before anything queued there later.
+constexpr int kForks = 4;
+struct Forks {
+    int device = -1;
+    cudaStream_t s[kForks] = {};
+    cudaEvent_t start = nullptr;
+    cudaEvent_t done[kForks] = {};
+};
+std::mutex g_fork_mu;  // also serialises the use of one device's events
+std::vector<Forks> g_forks;
+
+Forks *forks_for(int dev) {
+    for (Forks &f : g_forks)
+        if (f.device == dev) return &f;
+    Forks f;
+    f.device = dev;
+    bool ok = cudaEventCreateWithFlags(&f.start, cudaEventDisableTiming) == cudaSuccess;
+    for (int k = 0; k < kForks && ok; ++k)
+        ok = cudaStreamCreateWithFlags(&f.s[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&f.done[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    g_forks.push_back(f);
+    return &g_forks.back();
+}
+
+// FP32 images of a batch, spread over the fork streams and joined back.
+int fp32_batch_forked(const bf_item *items, int n, cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_fork_mu);
+    Forks *f = forks_for(dev);
+    if (!f) return BF_ERR_NOMEM;
+    int rc = bf::cuda_err(cudaEventRecord(f->start, s));
+    for (int k = 0; k < kForks && rc == BF_OK; ++k) rc = bf::cuda_err(cudaStreamWaitEvent(f->s[k], f->start, 0));
+    if (rc != BF_OK) return rc;
+    for (int i = 0, j = 0; i < n && rc == BF_OK; ++i) {
+        const bf_item &it = items[i];
+        if (it.H == 0 || it.W == 0) continue;
+        rc = bf::launch_fp32(*it.plan, it.in, it.out, it.H, it.W, it.pitch, f->s[j++ % kForks]);
+    }
+    for (int k = 0; k < kForks; ++k) {  // join even after an error, so the caller's stream stays ordered
+        const int r1 = bf::cuda_err(cudaEventRecord(f->done[k], f->s[k]));
+        const int r2 = bf::cuda_err(cudaStreamWaitEvent(s, f->done[k], 0));
+        if (rc == BF_OK) rc = r1 != BF_OK ? r1 : r2;
+    }
+    return rc;
+}
+}  // namespace
+
 extern "C" int bf_filter_batch(const bf_item *items, int n, int variant, void *stream) {
     if (n < 0 || (n > 0 && !items)) return BF_ERR_ARG;
     for (int i = 0; i < n; ++i) {
@@ -118,6 +174,7 @@ extern "C" int bf_filter_batch(const bf_item *items, int n, int variant, void *s
         return bf::tc_launch_batch(items, n, variant, scratch, st, s);
     }
     if (variant != BF_FP32 && variant != BF_FP32_RECURSIVE) return BF_ERR_ARG;
+    if (variant == BF_FP32 && n > 1) return fp32_batch_forked(items, n, s);
     for (int i = 0; i < n; ++i) {
         const bf_item &it = items[i];
         if (it.H == 0 || it.W == 0) continue;
