@@ -213,7 +213,14 @@ def _w_4k() -> Workload:
                     "voronoi", 10.0, seed=3000)
 
 
-WORKLOADS = {"small": _w_small, "mid": _w_mid, "4k": _w_4k}
+def _w_d6() -> Workload:
+    # six channels (the uneven batch's d = 6 images, e.g. two RGB frames stacked)
+    return Workload("d6_1024_voronoi_s5_K32", 1024, 1024, 6, 5.0,
+                    spd_cond(6, seed=4, lam_min_range=(30.0 ** 2, 40.0 ** 2), cond=5.0), 10, 32,
+                    "voronoi", 10.0, seed=3300)
+
+
+WORKLOADS = {"small": _w_small, "mid": _w_mid, "4k": _w_4k, "d6": _w_d6}
 
 
 def crop_origins(H: int, W: int, size: int = 256, n: int = 4, seed: int = 3100) -> list[tuple[int, int]]:
