@@ -269,16 +269,23 @@ def run_ours(args):
     kernel_ms = statistics.mean(per_step)
 
     # ---- end to end through the host-buffer entry point ----------------------
+    # Every step copies its input in from pinned host memory, filters and copies
+    # the result back; steps alternate between two streams so that one image's
+    # copies overlap the other's filtering (bf_filter_host_async).
     hin = torch.from_numpy(f).pin_memory().numpy()
-    hout = torch.empty(f.shape, dtype=torch.float32).pin_memory().numpy()
-    bf.bf_filter_host(plan, hin, hout, variant, sp)
-    e2e_steps = max(1, min(args.steps, 10))
+    io_streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    houts = [torch.empty(f.shape, dtype=torch.float32).pin_memory().numpy() for _ in io_streams]
+    for k, st in enumerate(io_streams):
+        bf.bf_filter_host_async(plan, hin, houts[k], variant, st.cuda_stream)
+    e2e_steps = max(2, min(args.steps, 10))
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        bf.bf_filter_host(plan, hin, hout, variant, sp)
+    for i in range(e2e_steps):
+        bf.bf_filter_host_async(plan, hin, houts[i % 2], variant, io_streams[i % 2].cuda_stream)
+    for st in io_streams:
+        st.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, dist)
     e2e_value = whole_job_mpx(ws, e2e_steps, pixels, e2e_s)
 
@@ -363,7 +370,9 @@ def run_ours(args):
         "plan_ms": plan_ms,
         "fp32_value": fp32_mpx,
         "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": int(f.nbytes),
-                "d2h_bytes_per_step": int(f.nbytes), "api": "bf_filter_host (pinned host buffers)"},
+                "d2h_bytes_per_step": int(f.nbytes), "api": "bf_filter_host_async, steps alternating over two streams (pinned host buffers)",
+                "note": "consecutive images overlap: copies run beside the other stream's kernel, and the "
+                        "next kernel fills the SMs the previous one's last tile wave leaves idle"},
         "gpu_launches": args.steps * (2 * math.ceil(w.K / 32) + 1 if variant == bf.BF_FP32_RECURSIVE else 1),
         "roofline": roof,
         "cpu_baseline": cpu,

@@ -217,6 +217,20 @@ int bf_filter_host(bf_plan_t plan, const float *in_host, float *out_host, int H,
 int bf_rgb_to_lab(const float *in, float *out, int H, int W, int pitch, void *stream);
 int bf_lab_to_rgb(const float *in, float *out, int H, int W, int pitch, void *stream);
 
+/*
+ * bf_filter_host_async -- bf_filter_host without the final synchronisation:
+ * the copy in, the filter and the copy out are queued on `stream` and the call
+ * returns.  For the copies to be asynchronous the host buffers must be pinned
+ * (cudaHostAlloc / cudaHostRegister); they must stay valid, and out_host must
+ * not be read, until the stream has reached this work (synchronise it or wait
+ * on an event recorded after the call).  Device buffers are per (device,
+ * stream), kept by the library and reused by the next call on the same stream,
+ * which the stream orders after this one; calls on different streams overlap
+ * (the copies of one with the filter of another).
+ */
+int bf_filter_host_async(bf_plan_t plan, const float *in_host, float *out_host, int H, int W, int variant,
+                         void *stream);
+
 /* Status word of the library's device-side guards (bounded waits, tile-queue
  * consistency) for work issued on `stream`; synchronises the stream, returns
  * BF_OK or the first BF_ERR_* recorded, and clears it. */

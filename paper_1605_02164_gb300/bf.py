@@ -86,6 +86,7 @@ def _load():
         lib.bf_filter_batch.argtypes = [ctypes.POINTER(bf_item), i, i, vp]
         lib.bf_filter_batch_noalloc.argtypes = [ctypes.POINTER(bf_item), i, i, vp]
         lib.bf_filter_host.argtypes = [vp, vp, vp, i, i, i, vp]
+        lib.bf_filter_host_async.argtypes = [vp, vp, vp, i, i, i, vp]
         lib.bf_rgb_to_lab.argtypes = [vp, vp, i, i, i, vp]
         lib.bf_lab_to_rgb.argtypes = [vp, vp, i, i, i, vp]
         lib.bf_last_status.argtypes = [vp]
@@ -214,6 +215,20 @@ def bf_lab_to_rgb(in_ptr: int, out_ptr: int, H: int, W: int, pitch: int, stream:
     """CIE 1976 L*a*b* -> sRGB (0..255), planar [3][H][pitch] device buffers (in place allowed)."""
     _check(_load().bf_lab_to_rgb(ctypes.c_void_p(in_ptr), ctypes.c_void_p(out_ptr), int(H), int(W), int(pitch),
                                  ctypes.c_void_p(stream)), "bf_lab_to_rgb")
+
+
+def bf_filter_host_async(plan: Plan, in_host: np.ndarray, out_host: np.ndarray, variant: int = BF_FP32,
+                         stream: int = 0) -> np.ndarray:
+    """Queues copy in, filter and copy out on `stream` and returns (host arrays
+    (d, H, W) float32, C-contiguous, pinned for asynchronous copies; out_host is
+    valid once the stream has reached this work)."""
+    for a in (in_host, out_host):
+        assert a.flags["C_CONTIGUOUS"] and a.dtype == np.float32 and a.shape == in_host.shape
+    d, H, W = in_host.shape
+    _check(_load().bf_filter_host_async(plan, ctypes.c_void_p(in_host.ctypes.data),
+                                        ctypes.c_void_p(out_host.ctypes.data), H, W, int(variant),
+                                        ctypes.c_void_p(stream)), "bf_filter_host_async")
+    return out_host
 
 
 def bf_last_status(stream: int = 0) -> int:

@@ -232,6 +232,69 @@ extern "C" int bf_filter_host(bf_plan_t p, const float *in_host, float *out_host
     return rc;
 }
 
+namespace {
+// Device buffers of bf_filter_host_async: one in/out pair per (device, stream),
+// grown on demand; a call is ordered after the previous one on its stream.
+struct IoSlot {
+    int device;
+    cudaStream_t stream;
+    void *ptr;
+    size_t bytes;
+};
+std::mutex g_io_mu;
+std::vector<IoSlot> g_io;
+
+void *io_buffers(cudaStream_t s, size_t bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_io_mu);
+    IoSlot *slot = nullptr;
+    for (IoSlot &sl : g_io)
+        if (sl.device == dev && sl.stream == s) slot = &sl;
+    if (slot && slot->bytes >= bytes) return slot->ptr;
+    if (!slot) {
+        g_io.push_back(IoSlot{dev, s, nullptr, 0});
+        slot = &g_io.back();
+    }
+    if (slot->ptr) {
+        cudaStreamSynchronize(s);  // queued copies may still use the old buffers
+        cudaFree(slot->ptr);
+        slot->ptr = nullptr;
+        slot->bytes = 0;
+    }
+    if (cudaMalloc(&slot->ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    slot->bytes = bytes;
+    return slot->ptr;
+}
+}  // namespace
+
+extern "C" int bf_filter_host_async(bf_plan_t p, const float *in_host, float *out_host, int H, int W, int variant,
+                                    void *stream) {
+    if (!p || H < 0 || W < 0) return BF_ERR_ARG;
+    if (H == 0 || W == 0) return BF_OK;
+    if (!in_host || !out_host) return BF_ERR_ARG;
+    const int pitch = (W + 3) & ~3;
+    const size_t img = (size_t)p->d * H * (size_t)pitch * sizeof(float);
+    const size_t half = (img + 255) / 256 * 256;
+    cudaStream_t s = (cudaStream_t)stream;
+    char *buf = (char *)io_buffers(s, 2 * half);
+    if (!buf) return BF_ERR_NOMEM;
+    float *din = (float *)buf, *dout = (float *)(buf + half);
+    const size_t plane_h = (size_t)H * W, plane_d = (size_t)H * pitch;
+    int rc = BF_OK;
+    for (int c = 0; c < p->d && rc == BF_OK; ++c)
+        rc = bf::cuda_err(cudaMemcpy2DAsync(din + c * plane_d, pitch * sizeof(float), in_host + c * plane_h,
+                                            W * sizeof(float), W * sizeof(float), H, cudaMemcpyHostToDevice, s));
+    if (rc == BF_OK) rc = bf_filter(p, din, dout, H, W, pitch, variant, stream);
+    for (int c = 0; c < p->d && rc == BF_OK; ++c)
+        rc = bf::cuda_err(cudaMemcpy2DAsync(out_host + c * plane_h, W * sizeof(float), dout + c * plane_d,
+                                            pitch * sizeof(float), W * sizeof(float), H, cudaMemcpyDeviceToHost, s));
+    return rc;
+}
+
 extern "C" int bf_last_status(void *stream) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BF_ERR_CUDA;

@@ -379,3 +379,21 @@ def test_tc_batch_equals_single_calls_and_oracle(bf, variant):
         assert np.array_equal(got, single)
         ref, res = _oracle_full(f, s, C, 10, K, seed)
         _check_tc(got, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
+
+
+def test_host_async_equals_host_entry_point(bf):
+    """bf_filter_host_async on two streams gives the results of bf_filter_host."""
+    w = synth.WORKLOADS["small"]()
+    f = w.image()[:, :90, :130].copy()
+    plan = bf.bf_plan(3, w.C, w.sigma_s, w.N, w.K, 21)
+    ref = bf.bf_filter_host(plan, f, None, bf.BF_FP16TC)
+    hin = torch.from_numpy(f).pin_memory().numpy()
+    outs = [torch.empty(f.shape, dtype=torch.float32).pin_memory().numpy() for _ in range(2)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i in range(4):
+        bf.bf_filter_host_async(plan, hin, outs[i % 2], bf.BF_FP16TC, streams[i % 2].cuda_stream)
+    for st in streams:
+        st.synchronize()
+    for o in outs:
+        assert np.array_equal(o, ref)
+    assert bf.bf_last_status(0) == bf.BF_OK
