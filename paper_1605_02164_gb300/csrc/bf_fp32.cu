@@ -29,7 +29,7 @@
 namespace bf {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kRC = 16;  // region rows per chunk
 constexpr int kBX = 32;  // output columns per tile
 
