@@ -79,3 +79,16 @@ def test_colour_transform_argument_checks(lib):
         assert fn(vp(0x10004), vp(0x20000), 4, 5, 8, None) == bf.BF_ERR_ALIGN
         assert fn(vp(0x10000), vp(0x20000), 4, 5, 6, None) == bf.BF_ERR_ALIGN  # pitch % 4
         assert fn(vp(0x10000), vp(0x10010), 4, 5, 8, None) == bf.BF_ERR_ARG   # partial overlap
+
+
+def test_host_entry_points_argument_checks(lib):
+    """bf_filter_host / bf_filter_host_async reject bad arguments before any CUDA call."""
+    from paper_1605_02164_gb300 import bf
+    L = bf.lib()
+    vp = ctypes.c_void_p
+    buf = (ctypes.c_float * 16)()
+    for fn in (L.bf_filter_host, L.bf_filter_host_async):
+        assert fn(None, buf, buf, 4, 4, 0, None) == bf.BF_ERR_ARG          # no plan
+        assert fn(vp(1), buf, buf, -1, 4, 0, None) == bf.BF_ERR_ARG        # negative size
+        assert fn(vp(1), None, buf, 4, 4, 0, None) == bf.BF_ERR_ARG        # null host buffer
+        assert fn(vp(1), buf, buf, 0, 4, 0, None) == bf.BF_OK              # empty image: no-op
