@@ -370,7 +370,7 @@ static void gauss_conv(const double complex *in, double complex *tmp, double com
  *   S = P / Z
  * The paper divides the complex sums.  The reading here takes real parts,
  * S_c = Re P_c / Re Z: the imaginary parts have zero expectation because Y is
- * symmetric about 0, and the spec filter is real.  Weights wt_t default
+ * symmetric about 0, and the filter being approximated is real.  Weights wt_t default
  * to 1/K (Eq. finalApproxY); other weights let the exhaustive expectation of
  * Prop. 2 be evaluated with the same code.
  * Outputs (any may be NULL except out): out d x H x W, Pre/Pim d x H x W,
