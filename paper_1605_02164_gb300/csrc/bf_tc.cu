@@ -667,6 +667,32 @@ int tc_fill(const bf_item &it, int variant, TcImg &g) {
     return BF_OK;
 }
 
+// One image alone: the tile height (a multiple of 16 rows, at most the one the
+// geometry allows) that minimises (waves of tiles over the SMs) x (16-row steps
+// per tile), so that a small image spreads over all SMs.  A pixel's arithmetic
+// does not depend on it: tile origins stay multiples of 16 rows.  Batches keep
+// the tallest tile; their queue balances the SMs.
+void tc_fit_waves(TcImg &g) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        return;
+    }
+    long long best_cost = -1;
+    int best = g.BY / 16;
+    for (int noc = g.BY / 16; noc >= 1; --noc) {
+        const long long tiles = (long long)g.tiles_x * cdiv(g.H, 16 * noc);
+        const long long cost = (tiles + nsm - 1) / nsm * cdiv(16 * noc + 2 * g.r, 16);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = noc;
+        }
+    }
+    g.BY = 16 * best;
+    g.nc = cdiv(g.BY + 2 * g.r, 16);
+}
+
 // Tile offsets and the shared-memory layout of an ordered table.
 void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
     int max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16, t = 0;
@@ -720,6 +746,7 @@ int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int
         ++m;
     }
     if (m == 0) return BF_OK;
+    if (m == 1) tc_fit_waves(tab[0]);
     std::stable_sort(tab, tab + m, cost_before);
     int total = 0;
     TcLayout lay{};
