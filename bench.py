@@ -45,8 +45,8 @@ def algorithmic_flops_per_pixel(d: int, r: int, K: int) -> float:
 # only stands for the kernel source it was taken on (sha1 of that file): after
 # any change to the source the bench reports null until a new capture.
 MEASURED_TRAFFIC = {
-    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "4d4451094ec540c5ce10f3fd55a427bdacd57d55",
-               "workload": "4k", "bytes_per_launch": 99.934e6 + 59.072e6,
+    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "74207a951f0d471314b13aac3983132de62da4f5",
+               "workload": "4k", "bytes_per_launch": 100.044e6 + 60.975e6,
                "capture": "ncu --set full of one launch on this workload (profiles/mcsf_tc_4k_s8_K128.md)"},
     "fp32rec": {"src": "paper_1605_02164_gb300/csrc/bf_recursive.cu", "sha1": "09714dfdb2c479e4e49e77f92076c4f2b2a37edb",
                 "bytes_per_pixel_term": (0.962 + 1.924 + 3.720 + 1.596) * 1e9 / (32 * 1024 * 1024),
