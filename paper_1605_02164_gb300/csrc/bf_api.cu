@@ -144,7 +144,7 @@ int fp32_batch_forked(const bf_item *items, int n, cudaStream_t s) {
     for (int i = 0, j = 0; i < n && rc == BF_OK; ++i) {
         const bf_item &it = items[i];
         if (it.H == 0 || it.W == 0) continue;
-        rc = bf::launch_fp32(*it.plan, it.in, it.out, it.H, it.W, it.pitch, f->s[j++ % kForks]);
+        rc = bf::launch_fp32(*it.plan, it.in, it.out, it.H, it.W, it.pitch, f->s[j++ % kForks], false);
     }
     for (int k = 0; k < kForks; ++k) {  // join even after an error, so the caller's stream stays ordered
         const int r1 = bf::cuda_err(cudaEventRecord(f->done[k], f->s[k]));

@@ -294,8 +294,34 @@ int fit_rows(int r, int H, int max_smem) {
     return by < BY ? by : BY;
 }
 
+// Tile height for the SMs (one CTA per SM): among multiples of 16 rows up to BY,
+// the one that minimises (waves of tiles) x (16-row chunks of phase and
+// horizontal work + 16-row blocks of vertical work per tile), so that a small
+// image spreads over all SMs.  A pixel's arithmetic does not depend on it.
+int fit_waves(int r, int H, int W, int BY) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0) {
+        cudaGetLastError();
+        return BY;
+    }
+    long long best = -1;
+    int best_by = BY;
+    for (int by = BY; by >= kRC; by -= kRC) {
+        const long long tiles = (long long)cdiv(W, kBX) * cdiv(H, by);
+        const long long cost = (tiles + nsm - 1) / nsm * (cdiv(by + 2 * r, kRC) + by / kRC);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_by = by;
+        }
+    }
+    return best_by;
+}
+
 template <int D, int G>
-int launch_dg(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int BY, cudaStream_t s) {
+int launch_dg(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int BY, cudaStream_t s,
+              bool alone) {
+    if (alone) BY = fit_waves(p.r, H, W, BY);
     const Geom g = make_geom<D, G>(p.r, BY);
     const size_t bytes = g.smem_floats * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(mcsf_fp32_kernel<D, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -311,30 +337,30 @@ int launch_dg(const bf_plan_s &p, const float *in, float *out, int H, int W, int
 // One pass per term when a tile of at least 32 rows fits, else two passes
 // (channel groups), else BF_ERR_UNSUPPORTED.
 template <int D>
-int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s) {
+int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s, bool alone) {
     int dev = 0, max_smem = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     const int by1 = fit_rows<D, 1>(p.r, H, max_smem);
-    if (by1 >= 32 || (by1 > 0 && by1 >= kRC * cdiv(H, kRC))) return launch_dg<D, 1>(p, in, out, H, W, pitch, by1, s);
+    if (by1 >= 32 || (by1 > 0 && by1 >= kRC * cdiv(H, kRC))) return launch_dg<D, 1>(p, in, out, H, W, pitch, by1, s, alone);
     const int by2 = fit_rows<D, 2>(p.r, H, max_smem);
-    if (by2 > 0) return launch_dg<D, 2>(p, in, out, H, W, pitch, by2, s);
-    if (by1 > 0) return launch_dg<D, 1>(p, in, out, H, W, pitch, by1, s);
+    if (by2 > 0) return launch_dg<D, 2>(p, in, out, H, W, pitch, by2, s, alone);
+    if (by1 > 0) return launch_dg<D, 1>(p, in, out, H, W, pitch, by1, s, alone);
     return BF_ERR_UNSUPPORTED;
 }
 
 }  // namespace
 
-int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s) {
+int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s, bool alone) {
     switch (p.d) {
-        case 1: return launch_d<1>(p, in, out, H, W, pitch, s);
-        case 2: return launch_d<2>(p, in, out, H, W, pitch, s);
-        case 3: return launch_d<3>(p, in, out, H, W, pitch, s);
-        case 4: return launch_d<4>(p, in, out, H, W, pitch, s);
-        case 5: return launch_d<5>(p, in, out, H, W, pitch, s);
-        case 6: return launch_d<6>(p, in, out, H, W, pitch, s);
-        case 7: return launch_d<7>(p, in, out, H, W, pitch, s);
-        case 8: return launch_d<8>(p, in, out, H, W, pitch, s);
+        case 1: return launch_d<1>(p, in, out, H, W, pitch, s, alone);
+        case 2: return launch_d<2>(p, in, out, H, W, pitch, s, alone);
+        case 3: return launch_d<3>(p, in, out, H, W, pitch, s, alone);
+        case 4: return launch_d<4>(p, in, out, H, W, pitch, s, alone);
+        case 5: return launch_d<5>(p, in, out, H, W, pitch, s, alone);
+        case 6: return launch_d<6>(p, in, out, H, W, pitch, s, alone);
+        case 7: return launch_d<7>(p, in, out, H, W, pitch, s, alone);
+        case 8: return launch_d<8>(p, in, out, H, W, pitch, s, alone);
         default: return BF_ERR_D_RANGE;
     }
 }

@@ -42,7 +42,10 @@ int noalloc_take_status();
 int check_image_args(const bf_plan_s *p, const float *in, const float *out, int H, int W, int pitch);
 
 // FP32 fused kernel (csrc/bf_fp32.cu).
-int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s);
+// alone: the image has the GPU to itself, so the tile height is fitted to the
+// SMs; images launched side by side (the batch) keep the tallest tile.
+int launch_fp32(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s,
+                bool alone = true);
 // Algorithm 1 with the recursive (Deriche) blur, FP32; scratch from stream_scratch.
 int launch_recursive(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, cudaStream_t s);
 
