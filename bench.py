@@ -373,7 +373,10 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(f.nbytes), "api": "bf_filter_host_async, steps alternating over two streams (pinned host buffers)",
                 "note": "consecutive images overlap: copies run beside the other stream's kernel, and the "
                         "next kernel fills the SMs the previous one's last tile wave leaves idle"},
-        "gpu_launches": args.steps * (2 * math.ceil(w.K / 32) + 1 if variant == bf.BF_FP32_RECURSIVE else 1),
+        # the recursive variant: two kernels per launch of tb terms (32, more for a
+        # narrow image: one column thread per term and column, ~77824 wanted) + the division
+        "gpu_launches": args.steps * (2 * math.ceil(w.K / min(w.K, max(32, math.ceil(77824 / w.W)))) + 1
+                                      if variant == bf.BF_FP32_RECURSIVE else 1),
         "roofline": roof,
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

@@ -32,13 +32,14 @@
 //             top to bottom, each row's blurred values combined at once with
 //             the centre cos/sin into the P / Z accumulators (Eqs. numerator,
 //             denom, real parts).  No barriers; loads run 2-4 rows ahead.
-//   Up to 32 terms run per launch (grid.y), each with its own X, V and P / Z
+//   32 or more terms run per launch (grid.y), each with its own X, V and P / Z
 //   slot, so more independent recursions are in flight and the sum over
 //   terms has a fixed order; a final kernel adds the slots and divides.
 // Scratch (library-owned, per stream, at most 24 GB): per term slot X and V
 // (2(d+1) planes each) and P/Z (d + 1 planes), FP32, rows padded to 32.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -71,7 +72,8 @@ Sections make_sections(double sigma) {
 
 constexpr int kRowT = 256;       // rec_rows: 32 rows x 8 channel groups
 constexpr int kColT = 128;       // rec_cols: one column per thread
-constexpr int kTermBatch = 32;   // terms per launch (grid.y)
+constexpr int kTermBatch = 32;   // terms per launch (grid.y), at least
+constexpr int kColThreadsTarget = 152 * 4 * kColT;  // column threads wanted per launch
 constexpr size_t kScratchCap = (size_t)24 << 30;  // bound on the per-stream scratch of this variant
 
 // Phase of one pixel (turns), kept as in the FP32 kernel: FP32 product with its
@@ -353,7 +355,9 @@ int launch_d(const bf_plan_s &p, const float *in, float *out, int H, int W, int 
     // Terms run kTermBatch at a time (grid.y), each with its own X, V and P/Z
     // slot: more independent recursions in flight, and a fixed summation order.
     const size_t per_term = (2 * term_stride + pz_stride) * sizeof(float);
-    int tb = kTermBatch;
+    // A narrow image gets more terms per launch, so that its column kernel
+    // (one thread per column and term) still has ~4 blocks per SM.
+    int tb = std::max(kTermBatch, (kColThreadsTarget + W - 1) / W);
     if (tb > p.K) tb = p.K;
     while (tb > 1 && (size_t)tb * per_term > kScratchCap) --tb;
     float *X = (float *)bf::stream_scratch(s, (size_t)tb * per_term);
