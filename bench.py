@@ -48,9 +48,9 @@ MEASURED_TRAFFIC = {
     "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "74207a951f0d471314b13aac3983132de62da4f5",
                "workload": "4k", "bytes_per_launch": 100.044e6 + 60.975e6,
                "capture": "ncu --set full of one launch on this workload (profiles/mcsf_tc_4k_s8_K128.md)"},
-    "fp32rec": {"src": "paper_1605_02164_gb300/csrc/bf_recursive.cu", "sha1": "09714dfdb2c479e4e49e77f92076c4f2b2a37edb",
-                "bytes_per_pixel_term": (0.962 + 1.924 + 3.720 + 1.596) * 1e9 / (32 * 1024 * 1024),
-                "capture": "ncu --set full of one row and one column launch (32 terms) on 1024x1024 "
+    "fp32rec": {"src": "paper_1605_02164_gb300/csrc/bf_recursive.cu", "sha1": "ae50e6fedcb753639417caa1d0166d124187c5a9",
+                "bytes_per_pixel_term": (1.966 + 3.941 + 7.515 + 3.207) * 1e9 / (64 * 1024 * 1024),
+                "capture": "ncu --set full of one row and one column launch (64 terms) on 1024x1024 "
                            "(profiles/mcsf_recursive_1024_s5_K64.md), scaled by pixels x terms"},
 }
 
