@@ -16,6 +16,7 @@ struct bf_plan_s {
     int device = 0;
     // device arrays (one allocation, `block`)
     void *block = nullptr;
+    bool pooled = false;       // block came from the library's stream-ordered plan pool
     float *nu_hi = nullptr;    // K*d: leading FP32 part of nu_t (turns)
     float *nu_lo = nullptr;    // K*d: FP32 remainder, nu = hi + lo to ~2^-48 relative
     double *nu64 = nullptr;    // K*d: FP64 nu_t

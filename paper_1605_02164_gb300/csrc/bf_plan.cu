@@ -10,7 +10,9 @@
 #include <math.h>
 #include <string.h>
 
+#include <mutex>
 #include <new>
+#include <vector>
 
 #include "bf_internal.cuh"
 
@@ -176,6 +178,58 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 }  // namespace
 
+namespace {
+// Per device: one stream for plan set-up and a stream-ordered memory pool for
+// plan blocks (allocation without a device-wide synchronisation; the pool
+// keeps up to 256 MB of freed blocks for reuse).  Plans are made one at a time.
+struct PlanRes {
+    int device;
+    cudaStream_t stream;
+    cudaMemPool_t pool;  // null: plain cudaMalloc
+};
+std::mutex g_plan_mu;
+std::vector<PlanRes> g_plan_res;
+
+PlanRes *plan_res(int dev) {
+    for (PlanRes &r : g_plan_res)
+        if (r.device == dev) return &r;
+    PlanRes r{dev, nullptr, nullptr};
+    if (cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if (cudaMemPoolCreate(&r.pool, &props) == cudaSuccess) {
+        uint64_t keep = 256ull << 20;
+        cudaMemPoolSetAttribute(r.pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+        cudaGetLastError();
+        r.pool = nullptr;
+    }
+    g_plan_res.push_back(r);
+    return &g_plan_res.back();
+}
+
+// Return a plan block to where it came from; the block is idle (the caller
+// has synchronised).
+cudaError_t release_block(bf_plan_s *p) {
+    if (!p->block) return cudaSuccess;
+    cudaError_t e = cudaSuccess;
+    if (p->pooled) {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        PlanRes *res = plan_res(p->device);
+        e = res ? cudaFreeAsync(p->block, res->stream) : cudaErrorUnknown;
+    } else {
+        e = cudaFree(p->block);
+    }
+    p->block = nullptr;
+    return e;
+}
+}  // namespace
+
 int make_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t seed, int whiten, int radius,
               bf_plan_t *out) {
     if (!out) return BF_ERR_ARG;
@@ -220,8 +274,19 @@ int make_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t see
     size_t off_C = align_up(off_tbf + p->taps_len * sizeof(uint16_t), 256);
     size_t off_ok = align_up(off_C + (size_t)d * d * sizeof(double), 256);
     size_t total = off_ok + 256;
-    if (cudaMalloc(&p->block, total) != cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    PlanRes *res = plan_res(p->device);
+    if (!res) {
+        delete p;
+        return BF_ERR_CUDA;
+    }
+    cudaStream_t s = res->stream;
+    p->pooled = res->pool != nullptr;
+    const cudaError_t ae = p->pooled ? cudaMallocFromPoolAsync(&p->block, total, res->pool, s)
+                                     : cudaMalloc(&p->block, total);
+    if (ae != cudaSuccess) {
         cudaGetLastError();
+        p->block = nullptr;
         delete p;
         return BF_ERR_NOMEM;
     }
@@ -254,14 +319,7 @@ int make_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t see
         memcpy(&tb[u], &bh, 2);
     }
 
-    cudaStream_t s;
     int rc = BF_OK;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        cudaFree(p->block);
-        delete p;
-        return BF_ERR_CUDA;
-    }
     int ok = 0;
     rc |= cuda_err(cudaMemcpyAsync(dC, C, sizeof(double) * d * d, cudaMemcpyHostToDevice, s));
     rc |= cuda_err(cudaMemcpyAsync(p->Y, p->Y_host.data(), sizeof(int32_t) * kd, cudaMemcpyHostToDevice, s));
@@ -274,17 +332,18 @@ int make_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t see
         plan_freqs_kernel<<<blocks, 256, 0, s>>>(d, K, N, whiten, dC, p->Y, p->nu64, p->nu_hi, p->nu_lo, dok);
         rc = cuda_err(cudaGetLastError());
     }
+    p->nu_host.resize(kd);
     if (rc == BF_OK) rc = cuda_err(cudaMemcpyAsync(&ok, dok, sizeof(int), cudaMemcpyDeviceToHost, s));
-    if (rc == BF_OK) rc = cuda_err(cudaStreamSynchronize(s));
+    if (rc == BF_OK)
+        rc = cuda_err(cudaMemcpyAsync(p->nu_host.data(), p->nu64, sizeof(double) * kd, cudaMemcpyDeviceToHost, s));
+    if (rc == BF_OK) rc = cuda_err(cudaStreamSynchronize(s));  // the one wait: the SPD check needs the kernel
     if (rc == BF_OK && !ok) rc = BF_ERR_NOT_SPD;
-    if (rc == BF_OK) {
-        p->nu_host.resize(kd);
-        rc = cuda_err(cudaMemcpy(p->nu_host.data(), p->nu64, sizeof(double) * kd, cudaMemcpyDeviceToHost));
-    }
-    cudaStreamDestroy(s);
     if (rc != BF_OK) {
         cudaGetLastError();
-        cudaFree(p->block);
+        cudaStreamSynchronize(s);
+        if (p->pooled) cudaFreeAsync(p->block, s);
+        else cudaFree(p->block);
+        cudaGetLastError();
         delete p;
         return rc;
     }
@@ -323,8 +382,15 @@ extern "C" int bf_plan_info(bf_plan_t p, int *d, int *K, int *N, int *radius, do
 
 extern "C" int bf_plan_destroy(bf_plan_t p) {
     if (!p) return BF_ERR_ARG;
-    int rc = BF_OK;
-    if (p->block) rc = bf::cuda_err(cudaFree(p->block));
+    // Wait for the device first, as cudaFree would: a filtering call still in
+    // flight on any stream finishes before the block goes back to the pool.
+    int prev = -1;
+    cudaGetDevice(&prev);
+    if (prev != p->device) cudaSetDevice(p->device);
+    int rc = bf::cuda_err(cudaDeviceSynchronize());
+    const int rc2 = bf::cuda_err(bf::release_block(p));
+    if (rc == BF_OK) rc = rc2;
+    if (prev >= 0 && prev != p->device) cudaSetDevice(prev);
     delete p;
     return rc;
 }

@@ -4,7 +4,9 @@ budget.
 Requests (one image each, with its own d, sigma_s, C, N, K, seed) arrive at any
 time.  The server
   * keeps plans (sampled, whitened frequency lists) resident on the device in
-    an LRU cache keyed by (d, C, sigma_s, N, K, seed, whitening);
+    an LRU cache keyed by (d, C, sigma_s, N, K, seed, whitening); a plan evicted
+    from it is destroyed only once the device is idle (destroying a plan waits
+    for the device), or when many have piled up;
   * admits queued requests in arrival order while the device memory they need
     (their output buffer; inputs are the caller's) fits in the budget, and
     rejects a request larger than the whole budget (BF_ERR_BUDGET) or one whose
@@ -63,7 +65,7 @@ class Request:
 
 class Server:
     def __init__(self, budget_bytes: int = 40 << 30, streams: int = 2, max_batch: int = 64,
-                 variant: int = bf.BF_FP16TC, plan_cache: int = 256, device: int = 0):
+                 variant: int = bf.BF_FP16TC, plan_cache: int = 1024, device: int = 0):
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
@@ -76,6 +78,7 @@ class Server:
         self.queue: collections.deque[Request] = collections.deque()
         self.plans: collections.OrderedDict = collections.OrderedDict()
         self.plan_cache = plan_cache
+        self.retired: list[bf.Plan] = []        # evicted plans waiting for an idle device
         self.lock = threading.Lock()
         self.cv = threading.Condition(self.lock)
         self.closed = False
@@ -92,10 +95,17 @@ class Server:
             p = bf.bf_plan(d, C, sigma_s, N, K, seed, whiten)
             self.plans[key] = p
             while len(self.plans) > self.plan_cache:
-                self.plans.popitem(last=False)  # its handle is released when unreferenced
+                self.retired.append(self.plans.popitem(last=False)[1])
+            if len(self.retired) > self.plan_cache:
+                self._release_retired()
         else:
             self.plans.move_to_end(key)
         return p
+
+    def _release_retired(self):
+        for p in self.retired:
+            p.close()
+        self.retired.clear()
 
     # -- client side -------------------------------------------------------------------
     def submit(self, req: Request) -> Request:
@@ -203,6 +213,8 @@ class Server:
                 if batch:
                     self._launch(free[0], batch)
                     progressed = True
+            if self.retired and all(b is None for b in self.busy):
+                self._release_retired()  # nothing in flight: the waits cost nothing
             with self.cv:
                 idle = not self.queue and all(b is None for b in self.busy)
                 if self.closed and idle:
