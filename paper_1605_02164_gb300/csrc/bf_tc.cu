@@ -38,7 +38,14 @@
 namespace bf {
 namespace {
 
-constexpr int kT = 512;  // 16 warps: channels, transpose, combine; lane 0 of warps 0 and 4-7 also issue MMAs
+constexpr int kComputeWarps = 16;  // channels, transpose, combine
+constexpr int kComputeThreads = 32 * kComputeWarps;
+constexpr int kT = kComputeThreads + 128;  // + one warpgroup that issues the MMAs
+// Registers per thread: the launch gives every thread kRegsLaunch (ptxas, from
+// the launch bounds); the issuer warpgroup then drops to kRegsIssuer and the
+// compute warps rise to kRegsCompute.  The shares must fit in the launch's total.
+constexpr int kRegsLaunch = 96, kRegsIssuer = 32, kRegsCompute = 112;
+static_assert(128 * kRegsIssuer + kComputeThreads * kRegsCompute <= kT * kRegsLaunch, "register split");
 constexpr int kBX = 64;        // output columns per tile
 constexpr int kNC = 8;         // 16-row chunks per region (128 rows)
 constexpr int kNOC = 5;        // output chunks (of 16 rows) per tile at most
@@ -67,13 +74,14 @@ struct TcImg {
     int Kw, ksteps;         // vertical pass: window rows 16 (lag + 1), K-steps of 16
     int Kw1, ks1;           // horizontal pass: 64 + 2r rounded up to 16, K-steps of 16
     int BY, nc, ringC;      // output rows per tile, 16-row chunks per term, centre-ring rows
-    int tiles_x, tile_begin, pad;
+    int tiles_x, tile_begin, ringA;  // ringA: rows of the blurred-row ring (Kw, or Kw + 16)
 };
 static_assert(sizeof(TcImg) == 96, "descriptor layout");
 
 // Shared-memory layout of a launch, sized for the largest window in it.
 struct TcLayout {
     uint32_t offA2, offB1, offB, offC, smem;
+    int spec;  // 1: every image has the geometry of the specialised kernel (8 chunks, lag 3, 80 rows)
 };
 
 // Launch control words kept in device scratch: [0] tile counter (zeroed by
@@ -124,6 +132,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
     }
     return false;
 }
+
+// Barrier of the compute warps only (named barrier 1); returns whether any of
+// them passed `v` true, so that all take the same branch after it.
+__device__ __forceinline__ bool compute_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
+        "barrier.cta.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(kComputeThreads)
+        : "memory");
+    return r != 0;
+}
+
+// Step barrier (named barrier 2, all kT threads): the compute warps arrive
+// without waiting, the issuer warps wait in hardware (no polling).
+__device__ __forceinline__ void step_arrive() { asm volatile("bar.arrive 2, %0;" ::"n"(kT) : "memory"); }
+__device__ __forceinline__ void step_wait() { asm volatile("bar.sync 2, %0;" ::"n"(kT) : "memory"); }
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -198,41 +224,57 @@ __device__ __forceinline__ uint32_t bits(T v) {
     return u;
 }
 
-// Persistent kernel: each CTA keeps its tensor memory and pops tiles (of all
-// images) from a device work counter until the queue is empty.
-// Per tile, a software pipeline over the flat sequence of (term, 16-row chunk)
-// steps s = k * nc + c.  All 16 warps in step s
+// Persistent kernel, warp-specialised.  Warps 0-15 do the CUDA-core work
+// (channels, D1 -> ring, combine); warps 16-19 only issue MMAs.  A
+// tcgen05.mma holds its issuing thread until the tensor pipe takes it, so an
+// issuer spends most of the pipe's time for a step waiting (~1000 cycles at
+// r = 24); on warps of their own those waits no longer hold up the step's
+// CUDA-core work.  The issuer warpgroup gives up registers (setmaxnreg) so
+// that the compute warps keep kRegsCompute.
+// Each CTA keeps its tensor memory and pops tiles (of all images) from a
+// device work counter until the queue is empty.  Per tile, a software
+// pipeline over the flat sequence of (term, 16-row chunk) steps
+// s = k * nc + c.  The compute warps in step s
 //   1  build the channels of chunk s+1 (A) into the A1 buffer not being read,
-//   1b wait for the vertical MMAs issued in step s-1 and combine them (C),
+//   1b wait for the vertical MMAs issued after step s-1 and combine them (C),
 //   2  wait for the horizontal MMAs of chunk s and move D1 into the ring (X),
-//   3  meet at one barrier;
-// then lane 0 of warp 0 issues the horizontal MMAs of chunk s+1 (one chain of
-// N = 64, K = 64 + 2r) and, when chunk s completes 16 output rows, lane 0 of
-// warps 4-7 each issue one vertical M-tile (N = 16, K = 16 + 16 ceil(2r/16)).
-// Each MMA group runs while the warps do a full step of other work.
+//   3  meet at a compute-only barrier, after which one thread arrives on the
+//      step barrier;
+// then the issuer warps issue, when chunk s completes 16 output rows, the 4
+// vertical M-tiles (one chain of N = 16, K = 16 + 16 ceil(2r/16) per warp),
+// and the horizontal MMAs of chunk s+1 (one chain of N = 64, K = 64 + 2r,
+// warp 16).  Each MMA group runs while the compute warps do a step of work.
 // TMEM: region f 0..383, D1 384..447, D2 448..511 (single-buffered: each is
 // read back before the group that rewrites it is issued).
-template <bool BF16>
+// NCT > 0 specialises the compute warps' step loop to a geometry of NCT chunks
+// per term, lag LAGT and NOBT output chunks per tile, with the centre ring
+// 16 NCT rows long: the chunk loop is unrolled and every ring slot, buffer
+// parity and output chunk of a step is a compile-time constant.  NCT = 0 is
+// the general loop (any geometry the tile scheme holds).
+template <bool BF16, int NCT, int LAGT, int NOBT>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
                    int *__restrict__ status, TcLayout lay) {
     constexpr int NOC = kNOC;
     using P2 = Pair<BF16>;
     extern __shared__ __align__(1024) uint8_t sm[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    // [0] horizontal MMAs done, [1] vertical MMAs done (4 issuers), [2..5]
+    // drain barrier of each issuer warp
+    __shared__ __align__(8) uint64_t mbar[6];
     __shared__ uint32_t taddr_s;
-    __shared__ int abort_s, tile_s;
+    __shared__ int tile_s, cstop_s;
 
     uint8_t *A1 = sm;               // 2 x [mg 16][kg 16][8 rows][16 B]   K-major (double buffer)
-    uint8_t *A2 = sm + lay.offA2;   // [kg Kw/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
+    uint8_t *A2 = sm + lay.offA2;   // [kg ringA/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
     uint8_t *B1 = sm + lay.offB1;   // [kg Kw1/8][ng 8][8 n][16 B]  K-major band, horizontal pass (N = 64)
     uint8_t *B2 = sm + lay.offB;    // [kg Kw/8][ng 2][8 n][16 B]   K-major band, vertical pass (N = 16)
     float2 *ring = reinterpret_cast<float2 *>(sm + lay.offC);  // [ringC][64] centre (cos, sin), see ring_xor
     int *counter = ctrl;
 
-    // Warp w works on TMEM lane quarter q = w & 3 (the lanes it may access),
-    // x half h, and half e of the 8-pixel groups / of the 16 rows of a block.
-    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1, e = w >> 3;
+    // Compute warp w works on TMEM lane quarter q = w & 3 (the lanes it may
+    // access), x half h, and half e of the 8-pixel groups / of the 16 rows of a block.
+    const int tid = threadIdx.x, w = tid >> 5, l = tid & 31, q = w & 3, h = (w >> 2) & 1, e = (w >> 3) & 1;
+    const bool issuer = w >= kComputeWarps;
     const uint32_t lane_base = (uint32_t)(32 * q) << 16;
     // The thread owns pixels px0 .. px0 + 3 of its 8-pixel group; rows 8-15 take
     // the other half than rows 0-7 so that the 8-byte stores of a half-warp into
@@ -250,49 +292,149 @@ __global__ void __launch_bounds__(kT, 1)
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[0])) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(&mbar[1])) : "memory");  // 4 issuers
+        for (int i = 2; i < 6; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[i])) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        abort_s = 0;
+        cstop_s = 0;
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = taddr_s;
-    const uint64_t dA1 = sdesc(smem_u32(A1), 128, 2048);   // K-major: LBO = next K group, SBO = next 8 rows
-    const uint64_t dB1 = sdesc(smem_u32(B1), 1024, 128);
-    const uint64_t dA2 = sdesc(smem_u32(A2), 8192, 128);   // MN-major: LBO = next K group, SBO = next 8 columns
-    const uint64_t dB2 = sdesc(smem_u32(B2), 256, 128);
-    const uint32_t id1 = idesc(BF16 ? 1u : 0u, 0u, 64u);
-    const uint32_t id2 = idesc(BF16 ? 1u : 0u, 1u, 16u);
-    uint32_t ph1 = 0, ph2 = 0;  // barrier phases carry over from tile to tile
-    int band_r = -1;            // window radius the Toeplitz bands in smem were built for
-    bool timed_out = false;
+    bool aborted = false;  // every thread, after a barrier that agreed on it
+    // Each role runs its own tile loop, so that all of its code comes after its
+    // register change.  The barriers of the two loops pair up one to one: tile
+    // start; per step, the step barrier (compute -> issuers; when the compute
+    // warps stop they arrive once more with cstop_s set); the tile barrier, which
+    // also agrees on a stop; z buffer; tile end; final.
+    if (issuer) {
+        // 4 issuer warps x kRegsIssuer + 16 compute warps x kRegsCompute fit in
+        // the 20 x kRegsLaunch the block was launched with.
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegsIssuer));
+        for (;;) {
+            bool iss_stop = false;  // the compute warps stopped
+            __syncthreads();        // tile start (tile_s written by thread 0)
+            const int tile = tile_s;
+            if (tile >= total_tiles) break;
+            int im = 0;
+            while (im + 1 < n_imgs && __ldg(&imgs[im + 1].tile_begin) <= tile) ++im;
+            const TcImg &gg = imgs[im];
+            const int K = gg.K, NCr = gg.nc, lag = gg.lag, BY = gg.BY;
+            const int S = K * NCr;
+            // ---- MMA issue --------------------------------------------------------------
+            const int ks1 = gg.ks1, ksteps = gg.ksteps, kgring = gg.ringA >> 3;
+            const uint64_t dA1 = sdesc(smem_u32(A1), 128, 2048);  // K-major: LBO = next K group, SBO = next 8 rows
+            const uint64_t dB1 = sdesc(smem_u32(B1), 1024, 128);
+            const uint64_t dA2 = sdesc(smem_u32(A2), 8192, 128);  // MN-major: LBO = next K group, SBO = next 8 columns
+            const uint64_t dB2 = sdesc(smem_u32(B2), 256, 128);
+            const int t = w - kComputeWarps;  // vertical M-tile of this warp
+            // Descriptors are built per tile; operand offsets are added to the
+            // 14-bit start-address field (address >> 4).
+            auto issue_M1 = [&](int s) {
+                const uint64_t a = dA1 + (uint64_t)((s & 1) * (32768 >> 4));
+                const uint32_t id1 = idesc(BF16 ? 1u : 0u, 0u, 64u);
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                    if (ks < ks1) mma_f16(tmem + kColD1, a + 16 * ks, dB1 + 128 * ks, id1, ks > 0);
+                mma_commit(&mbar[0]);
+            };
+            auto issue_M2 = [&](int s_first) {
+                const uint32_t id2 = idesc(BF16 ? 1u : 0u, 1u, 16u);
+                const int kgb = (2 * s_first) % kgring;
+#pragma unroll
+                for (int ks = 0; ks < 5; ++ks)
+                    if (ks < ksteps) {
+                        int kg0 = kgb + 2 * ks;
+                        if (kg0 >= kgring) kg0 -= kgring;
+                        mma_f16(tmem + kColD2 + 16 * t, dA2 + (uint64_t)((kg0 * 8192 + t * 2048) >> 4),
+                                dB2 + 32 * ks, id2, ks > 0);
+                    }
+                mma_commit(&mbar[1]);
+            };
+            // prologue: chunk 0's channels are in A1[0] once the step barrier completes
+            step_wait();
+            if (cstop_s) {
+                iss_stop = true;
+                goto iss_tile_end;
+            }
+            if (t == 0 && l == 0) {
+                fence_after();
+                issue_M1(0);
+            }
+            __syncwarp();
+            {
+                int c = 0;
+                for (int s = 0; s < S; ++s) {
+                    const int oc = c - lag;
+                    const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
+                    step_wait();
+                    if (cstop_s) {
+                        iss_stop = true;
+                        goto iss_tile_end;
+                    }
+                    if (l == 0) {
+                        fence_after();
+                        if (do_m2) issue_M2(s - lag);  // needed first: the combine comes before D1 -> ring
+                        if (t == 0 && s + 1 < S) issue_M1(s + 1);
+                    }
+                    __syncwarp();
+                    if (++c == NCr) c = 0;
+                }
+            }
+        iss_tile_end:
+            fence_before();
+            if (__syncthreads_or(iss_stop)) {  // tile barrier
+                aborted = true;
+                break;
+            }
+            __syncthreads();  // z buffer
+            fence_before();
+            __syncthreads();  // tile end
+            fence_after();
+        }
+        if (aborted && l == 0) {
+            if (w == kComputeWarps) atomicCAS(status, 0, BF_ERR_TIMEOUT);
+            // drain: bounded wait for every MMA this thread issued (a barrier of its own, fresh phase)
+            mma_commit(&mbar[2 + (w - kComputeWarps)]);
+            mbar_wait(&mbar[2 + (w - kComputeWarps)], 0);
+        }
+        fence_before();
+        __syncthreads();  // final
+        return;
+    }
 
+    // ---- compute warps --------------------------------------------------------------------
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsCompute));
+    int band_r = -1;            // window radius the Toeplitz bands in smem were built for
+    uint32_t ph1 = 0, ph2 = 0;  // phases of mbar[0], mbar[1] (carry over from tile to tile)
     for (;;) {
-        // ---- next tile -------------------------------------------------------------
+        bool timed_out = false;  // a wait on the tensor core ran out
         if (tid == 0) tile_s = atomicAdd(counter, 1);
-        __syncthreads();
+        __syncthreads();  // tile start
         const int tile = tile_s;
         if (tile >= total_tiles) break;
         int im = 0;
         while (im + 1 < n_imgs && __ldg(&imgs[im + 1].tile_begin) <= tile) ++im;
         const TcImg g = imgs[im];
+        const int K = g.K, NCr = g.nc, lag = g.lag, BY = g.BY;
+        const int S = K * NCr;
         const float *__restrict__ in = g.in;
         float *__restrict__ out = g.out;
         const float *__restrict__ nu_hi = g.nu_hi;
-        const int H = g.H, W = g.W, pitch = g.pitch, K = g.K, r = g.r, BY = g.BY;
+        const int H = g.H, W = g.W, pitch = g.pitch, r = g.r;
         const int tl = tile - g.tile_begin;
         const int ty = tl / g.tiles_x, tx = tl - ty * g.tiles_x;
         const int tx0 = tx * kBX, ty0 = ty * BY;
         const int rx0 = tx0 - r, ry0 = ty0 - r;
         const size_t plane = (size_t)H * pitch;
 
-        if (r != band_r) {  // Toeplitz bands of the normalised taps (uniform across the CTA)
-            for (int i = tid; i < g.Kw1 * 64; i += kT) {
+        if (r != band_r) {  // Toeplitz bands of the normalised taps (uniform across the compute warps)
+            for (int i = tid; i < g.Kw1 * 64; i += kComputeThreads) {
                 const int k = i >> 6, n = i & 63, u = k - n;
                 const uint16_t v = (u >= 0 && u <= 2 * r) ? g.taps[u] : (uint16_t)0;
                 *reinterpret_cast<uint16_t *>(B1 + ((k >> 3) * 8 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
             }
-            for (int i = tid; i < g.Kw * 16; i += kT) {
+            for (int i = tid; i < g.Kw * 16; i += kComputeThreads) {
                 const int k = i >> 4, n = i & 15, u = k - n;
                 const uint16_t v = (u >= 0 && u <= 2 * r) ? g.taps[u] : (uint16_t)0;
                 *reinterpret_cast<uint16_t *>(B2 + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
@@ -338,7 +480,6 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
             for (int j = 0; j < 8; ++j) acc[o][j] = 0.f;
 
-        const int NCr = g.nc;  // 16-row chunks per term: ceil((BY + 2r) / 16) <= 8
         uint8_t *const dstA = A1 + xg * 128 + (row & 7) * 16 + (row >> 3) * 2048 + 2 * px0;
         // Ring columns of this thread's 4 pixels: the XOR depends on the ring row
         // only through (row - r) & 7, a constant of the tile.
@@ -350,9 +491,7 @@ __global__ void __launch_bounds__(kT, 1)
             nr1 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k + 1);
             nr2 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k + 2);
         };
-        const int S = K * NCr;
         int pend_oc = -1, pend_slot = 0;
-        const int kgring = g.Kw >> 3;
 
         // A: channels of flat step s (chunk c of the term whose frequency is in
         // nr0..nr2) into A1[s & 1]; slot16 = 16 s mod ringC.
@@ -376,9 +515,9 @@ __global__ void __launch_bounds__(kT, 1)
                     const int j = 2 * p + u;
                     // phase in radians; FP32 keeps its error near 1e-5 rad for |phase| <
                     // 100, far below the 16-bit rounding of the channels
-                    const float t = fmaf(nr0, f0[j], fmaf(nr1, f1[j], nr2 * f2[j]));
+                    const float tt = fmaf(nr0, f0[j], fmaf(nr1, f1[j], nr2 * f2[j]));
                     float s_, c_;
-                    __sincosf(t, &s_, &c_);
+                    __sincosf(tt, &s_, &c_);
                     const bool v = (vm >> j) & 1u;
                     cv[u] = v ? c_ : 0.f;
                     sv[u] = v ? s_ : 0.f;
@@ -465,103 +604,116 @@ __global__ void __launch_bounds__(kT, 1)
             }
         };
 
-        // MMA issue.  Descriptors are built once per CTA; operand offsets are
-        // added to the 14-bit start-address field (address >> 4).
-        auto issue_M1 = [&](int s) {
-            const uint64_t a = dA1 + (uint64_t)((s & 1) * (32768 >> 4));
-#pragma unroll
-            for (int ks = 0; ks < 8; ++ks)
-                if (ks < g.ks1) mma_f16(tmem + kColD1, a + 16 * ks, dB1 + 128 * ks, id1, ks > 0);
-            mma_commit(&mbar[0]);
-        };
-        auto issue_M2 = [&](int s_first, int t) {  // M-tile t of the vertical pass
-            const int kgb = (2 * s_first) % kgring;
-#pragma unroll
-            for (int ks = 0; ks < 5; ++ks)
-                if (ks < g.ksteps) {
-                    int kg0 = kgb + 2 * ks;
-                    if (kg0 >= kgring) kg0 -= kgring;
-                    mma_f16(tmem + kColD2 + 16 * t, dA2 + (uint64_t)((kg0 * 8192 + t * 2048) >> 4), dB2 + 32 * ks, id2,
-                            ks > 0);
-                }
-            mma_commit(&mbar[1]);
+        // End of a step: every compute warp has finished the step's smem writes
+        // and TMEM reads (compute barrier), then all arrive on the step barrier.
+        // If any compute warp timed out, all of them stop together and tell the
+        // issuers through cstop_s.
+        auto step_done = [&]() -> bool {
+            fence_before();
+            fence_async_smem();
+            const bool stop = compute_sync_or(timed_out);
+            if (stop && tid == 0) cstop_s = 1;
+            step_arrive();
+            return !stop;
         };
 
         // ---- prologue ------------------------------------------------------------------
         load_nu(0);
         stage_A(0, 0, 0);
-        fence_async_smem();
-        __syncthreads();
-        if (w == 0 && l == 0) {
-            fence_after();
-            issue_M1(0);
-        }
+        if (!step_done()) goto cmp_tile_end;
 
-        // ---- pipeline ----------------------------------------------------------------------
-        // Step s is chunk c of term k; slotS = 16 s mod ringC and krS = 16 s mod Kw
-        // are carried from step to step (no division in the loop), as are the
-        // chunk, term and slot of step s + 1 (cA, kA, slotA).
-        int c = 0, kA = 0, cA = 0, slotS = 0, krS = 0;
-        for (int s = 0; s < S; ++s) {
-            const int oc = c - g.lag;
-            const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
-            if (++cA == NCr) {
-                cA = 0;
-                if (++kA < K) load_nu(kA);
+        if constexpr (NCT > 0) {
+            // ---- pipeline, specialised geometry -----------------------------------------------
+            // Step (k, c): slot 16 c of the centre ring (16 NCT rows), blurred-row
+            // ring rows 16 (c mod (LAGT + 1)) (NCT is a multiple of LAGT + 1), A1
+            // buffer c & 1 (NCT even), output chunk c - LAGT.
+            static_assert(NCT % 2 == 0 && NCT % (LAGT + 1) == 0 && NCT >= LAGT + 3 && NOBT <= NOC, "geometry");
+            for (int k = 0; k < K; ++k) {
+#pragma unroll
+                for (int c = 0; c < NCT; ++c) {
+                    if (c + 1 < NCT) {
+                        stage_A(c + 1, c + 1, 16 * (c + 1));
+                    } else if (k + 1 < K) {
+                        load_nu(k + 1);
+                        stage_A(0, 0, 0);
+                    }
+                    // output chunk completed by the previous step
+                    const int ocp = (c == 0 ? NCT - 1 : c - 1) - LAGT;
+                    if (ocp >= 0 && ocp < NOBT && (c > 0 || k > 0)) {
+                        if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                        ph2 ^= 1;
+                        fence_after();
+                        stage_C(ocp, 16 * ocp + 8 * e);
+                    }
+                    if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
+                    ph1 ^= 1;
+                    fence_after();
+                    stage_X(16 * (c % (LAGT + 1)));
+                    if (!step_done()) goto cmp_tile_end;
+                }
             }
-            int slotA = slotS + 16;
-            if (slotA >= g.ringC) slotA -= g.ringC;
-            if (s + 1 < S) stage_A(s + 1, cA, slotA);
+            if (NCT - 1 - LAGT >= 0 && NCT - 1 - LAGT < NOBT) {
+                if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                ph2 ^= 1;
+                fence_after();
+                stage_C(NCT - 1 - LAGT, 16 * (NCT - 1 - LAGT) + 8 * e);
+            }
+        } else {
+            // ---- pipeline ----------------------------------------------------------------------
+            // Step s is chunk c of term k; slotS = 16 s mod ringC and krS = 16 s mod Kw
+            // are carried from step to step (no division in the loop), as are the
+            // chunk, term and slot of step s + 1 (cA, kA, slotA).
+            {
+                int c = 0, kA = 0, cA = 0, slotS = 0, krS = 0;
+                for (int s = 0; s < S; ++s) {
+                    const int oc = c - lag;
+                    const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
+                    if (++cA == NCr) {
+                        cA = 0;
+                        if (++kA < K) load_nu(kA);
+                    }
+                    int slotA = slotS + 16;
+                    if (slotA >= g.ringC) slotA -= g.ringC;
+                    if (s + 1 < S) stage_A(s + 1, cA, slotA);
+                    if (pend_oc >= 0) {
+                        if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                        ph2 ^= 1;
+                        fence_after();
+                        stage_C(pend_oc, pend_slot);
+                        pend_oc = -1;
+                    }
+                    if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
+                    ph1 ^= 1;
+                    fence_after();
+                    stage_X(krS);
+                    if (!step_done()) goto cmp_tile_end;
+                    if (do_m2) {
+                        pend_oc = oc;
+                        // flat output row 16 (s - lag) + 8 e, mod ringC (16 lag < ringC)
+                        int sl = slotS - 16 * lag + 8 * e;
+                        if (sl < 0) sl += g.ringC;
+                        if (sl >= g.ringC) sl -= g.ringC;
+                        pend_slot = sl;
+                    }
+                    c = cA;
+                    slotS = slotA;
+                    krS += 16;
+                    if (krS == g.ringA) krS = 0;
+                }
+            }
             if (pend_oc >= 0) {
                 if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
                 ph2 ^= 1;
                 fence_after();
                 stage_C(pend_oc, pend_slot);
-                pend_oc = -1;
             }
-            if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
-            ph1 ^= 1;
-            fence_after();
-            stage_X(krS);
-            fence_before();
-            fence_async_smem();
-            if (timed_out) abort_s = 1;
-            __syncthreads();
-            if (abort_s) goto cleanup;
-            if (l == 0 && (w == 0 || (w >= 4 && w < 8 && do_m2))) {
-                fence_after();
-                if (w == 0) {
-                    if (s + 1 < S) issue_M1(s + 1);
-                } else {
-                    issue_M2(s - g.lag, w - 4);
-                }
-            }
-            __syncwarp();
-            if (do_m2) {
-                pend_oc = oc;
-                // flat output row 16 (s - lag) + 8 e, mod ringC (16 lag < ringC)
-                int sl = slotS - 16 * g.lag + 8 * e;
-                if (sl < 0) sl += g.ringC;
-                if (sl >= g.ringC) sl -= g.ringC;
-                pend_slot = sl;
-            }
-            c = cA;
-            slotS = slotA;
-            krS += 16;
-            if (krS == g.Kw) krS = 0;
         }
-        if (pend_oc >= 0) {
-            if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
-            ph2 ^= 1;
-            fence_after();
-            stage_C(pend_oc, pend_slot);
-        }
-        if (timed_out) abort_s = 1;
-        fence_before();
-        __syncthreads();
-        if (abort_s) goto cleanup;
-
         // ---- P / Z ----------------------------------------------------------------
+        fence_before();
+        if (__syncthreads_or(timed_out)) {  // tile barrier, with the issuers
+            aborted = true;
+            break;
+        }
         {
             float *zbuf = reinterpret_cast<float *>(sm + lay.offC);  // [BY][64], reuses the centre ring
             const int x = 32 * h + l;
@@ -572,7 +724,7 @@ __global__ void __launch_bounds__(kT, 1)
                     for (int j = 0; j < 8; ++j)
                         if (16 * o + 8 * e + j < BY) zbuf[(16 * o + 8 * e + j) * kBX + x] = acc[o][j];
             }
-            __syncthreads();
+            __syncthreads();  // z buffer
             const int gx = tx0 + x;
             if (q < 3 && gx < W) {
 #pragma unroll
@@ -586,21 +738,20 @@ __global__ void __launch_bounds__(kT, 1)
             }
         }
         fence_before();
-        __syncthreads();  // zbuf, ring and TMEM are reused by the next tile
+        __syncthreads();  // tile end: zbuf, ring and TMEM are reused by the next tile
         fence_after();
-    }
-
-cleanup:
-    if (abort_s && l == 0 && (w == 0 || (w >= 4 && w < 8))) {
-        if (w == 0) atomicCAS(status, 0, BF_ERR_TIMEOUT);
-        // drain: bounded wait for every MMA this thread issued (fresh barrier phase)
-        mma_commit(&mbar[0]);
-        mbar_wait(&mbar[0], ph1);
+        continue;
+    cmp_tile_end:  // the compute warps stopped inside the step loop (all of them, see step_done)
+        fence_before();
+        __syncthreads_or(1);  // tile barrier
+        aborted = true;
+        break;
     }
     fence_before();
-    __syncthreads();
+    __syncthreads();  // final
     fence_after();
     if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    (void)aborted;
 }
 
 // ---------------------------------------------------------------------------------
@@ -612,6 +763,7 @@ bool tc_geometry(int r, TcImg &g) {
     g.r = r;
     g.lag = cdiv(2 * r, 16);
     g.Kw = 16 * (g.lag + 1);
+    g.ringA = g.Kw;
     g.ksteps = g.Kw / 16;
     g.Kw1 = 16 * cdiv(kBX + 2 * r, 16);
     g.ks1 = g.Kw1 / 16;
@@ -626,10 +778,10 @@ bool tc_geometry(int r, TcImg &g) {
     return true;
 }
 
-TcLayout tc_layout(int max_Kw, int max_Kw1, int max_ringC, int max_BY) {
+TcLayout tc_layout(int max_ringA, int max_Kw, int max_Kw1, int max_ringC, int max_BY) {
     TcLayout L{};
     L.offA2 = 65536;
-    L.offB1 = L.offA2 + (uint32_t)(max_Kw / 8) * 8192;
+    L.offB1 = L.offA2 + (uint32_t)(max_ringA / 8) * 8192;
     L.offB = L.offB1 + (uint32_t)max_Kw1 * 128;
     L.offC = (L.offB + (uint32_t)max_Kw * 32 + 127) & ~127u;
     const uint32_t ring_bytes = (uint32_t)max_ringC * kBX * 8;
@@ -693,10 +845,16 @@ void tc_fit_waves(TcImg &g) {
     g.nc = cdiv(g.BY + 2 * g.r, 16);
 }
 
-// Tile offsets and the shared-memory layout of an ordered table.
+// Tile offsets and the shared-memory layout of an ordered table.  When every
+// image has the geometry of the specialised kernel (r = 17..24 with 80-row
+// tiles: 8 chunks per term, lag 3), its centre ring takes 128 rows.
 void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
-    int max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16, t = 0;
+    bool spec = true;
+    for (int i = 0; i < m; ++i) spec = spec && tab[i].nc == 8 && tab[i].lag == 3 && tab[i].BY == 80;
+    int max_ringA = 16, max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16, t = 0;
     for (int i = 0; i < m; ++i) {
+        if (spec) tab[i].ringC = 128;
+        max_ringA = std::max(max_ringA, tab[i].ringA);
         tab[i].tile_begin = t;
         t += tab[i].tiles_x * cdiv(tab[i].H, tab[i].BY);
         max_Kw = std::max(max_Kw, tab[i].Kw);
@@ -705,7 +863,8 @@ void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
         max_BY = std::max(max_BY, tab[i].BY);
     }
     *total = t;
-    *lay = tc_layout(max_Kw, max_Kw1, max_ringC, max_BY);
+    *lay = tc_layout(max_ringA, max_Kw, max_Kw1, max_ringC, max_BY);
+    lay->spec = spec ? 1 : 0;
 }
 
 // Launch over a table already in device memory.  The table is ordered by
@@ -717,7 +876,19 @@ int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *statu
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if ((int)lay.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
-    auto kern = variant == BF_BF16TC ? mcsf_tc_kernel<true> : mcsf_tc_kernel<false>;
+    void (*kern)(const TcImg *, int, int, int *, int *, TcLayout);
+    if (lay.spec)
+        kern = variant == BF_BF16TC ? mcsf_tc_kernel<true, 8, 3, 5> : mcsf_tc_kernel<false, 8, 3, 5>;
+    else
+        kern = variant == BF_BF16TC ? mcsf_tc_kernel<true, 0, 0, 0> : mcsf_tc_kernel<false, 0, 0, 0>;
+    // The register split inside the kernel assumes the launch gives each thread
+    // kRegsLaunch registers; with fewer the compute warps' request could not be met.
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
+    if (fa.numRegs != kRegsLaunch) return BF_ERR_UNSUPPORTED;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.smem) != cudaSuccess) {
         cudaGetLastError();
         return BF_ERR_CUDA;
