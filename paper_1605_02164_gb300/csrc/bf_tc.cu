@@ -81,8 +81,20 @@ static_assert(sizeof(TcImg) == 96, "descriptor layout");
 // Shared-memory layout of a launch, sized for the largest window in it.
 struct TcLayout {
     uint32_t offA2, offB1, offB, offC, smem;
-    int spec;  // 1: every image has the geometry of the specialised kernel (8 chunks, lag 3, 80 rows)
+    int spec;  // index + 1 into kSpecGeom when every image has that geometry, else 0
 };
+
+// Geometries with a specialised step loop: the default tile of the lag classes
+// r = 1..8, 9..16 and 17..24; the 32-row tiles a 512 x 512 image takes alone at
+// r = 1..8 and 9..16 (two-term centre ring); the 64-row tile of a 1024 x 1024
+// image alone at r = 9..16.  (r = 25..32 keeps the general loop: a 128-row
+// centre ring would take the shared memory past 227 KB.)
+constexpr int kNumSpec = 6;
+struct SpecGeom {
+    int nc, lag, BY, terms;
+};
+constexpr SpecGeom kSpecGeom[kNumSpec] = {{6, 1, 80, 1}, {7, 2, 80, 1}, {8, 3, 80, 1},
+                                          {3, 1, 32, 2}, {4, 2, 32, 2}, {6, 2, 64, 1}};
 
 // Launch control words kept in device scratch: [0] tile counter (zeroed by
 // the copy that uploads the image table before every launch).
@@ -248,10 +260,11 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // read back before the group that rewrites it is issued).
 // NCT > 0 specialises the compute warps' step loop to a geometry of NCT chunks
 // per term, lag LAGT and NOBT output chunks per tile, with the centre ring
-// 16 NCT rows long: the chunk loop is unrolled and every ring slot, buffer
-// parity and output chunk of a step is a compile-time constant.  NCT = 0 is
-// the general loop (any geometry the tile scheme holds).
-template <bool BF16, int NCT, int LAGT, int NOBT>
+// 16 NCT PT rows long (PT terms): the chunk loop is unrolled and every ring
+// slot and output chunk of a step is a compile-time constant (plus a per-term
+// base when PT = 2).  NCT = 0 is the general loop (any geometry the tile
+// scheme holds).
+template <bool BF16, int NCT, int LAGT, int NOBT, int PT>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
                    int *__restrict__ status, TcLayout lay) {
@@ -624,31 +637,48 @@ __global__ void __launch_bounds__(kT, 1)
 
         if constexpr (NCT > 0) {
             // ---- pipeline, specialised geometry -----------------------------------------------
-            // Step (k, c): slot 16 c of the centre ring (16 NCT rows), blurred-row
-            // ring rows 16 (c mod (LAGT + 1)) (NCT is a multiple of LAGT + 1), A1
-            // buffer c & 1 (NCT even), output chunk c - LAGT.
-            static_assert(NCT % 2 == 0 && NCT % (LAGT + 1) == 0 && NCT >= LAGT + 3 && NOBT <= NOC, "geometry");
+            // Step (k, c): centre-ring slot tb(k) + 16 c, tb(k) = 16 NCT (k mod PT),
+            // output chunk c - LAGT; the A1 buffer (k NCT + c) & 1 and the
+            // blurred-row ring rows 16 ((k NCT + c) mod (LAGT + 1)) are constants
+            // too when NCT is even / a multiple of LAGT + 1, else they are carried
+            // from step to step.  The centre-ring rows a step writes (chunk c + 1,
+            // or chunk 0 of the next term) never meet the rows it combines (chunk
+            // c - 1 - LAGT, or the previous term's last): NCT >= LAGT + 3 keeps them
+            // apart in a one-term ring, PT = 2 puts consecutive terms in different halves.
+            static_assert((PT == 1 && NCT >= LAGT + 3) || (PT == 2 && NCT >= LAGT + 1), "geometry");
+            static_assert(NOBT <= NOC, "geometry");
+            constexpr bool kParConst = NCT % 2 == 0, kRingConst = NCT % (LAGT + 1) == 0;
+            auto tbase = [&](int kk) { return PT == 2 ? (kk & 1) * 16 * NCT : 0; };
+            int krS = 0;  // 16 s mod Kw when it is not a constant
             for (int k = 0; k < K; ++k) {
+                const int kpar = kParConst ? 0 : (k & 1);
+                const int tb = tbase(k);
 #pragma unroll
                 for (int c = 0; c < NCT; ++c) {
                     if (c + 1 < NCT) {
-                        stage_A(c + 1, c + 1, 16 * (c + 1));
+                        stage_A(kpar + c + 1, c + 1, tb + 16 * (c + 1));
                     } else if (k + 1 < K) {
                         load_nu(k + 1);
-                        stage_A(0, 0, 0);
+                        stage_A(kParConst ? 0 : (k + 1) & 1, 0, tbase(k + 1));
                     }
-                    // output chunk completed by the previous step
+                    // output chunk completed by the previous step (of term k - 1 when c = 0)
                     const int ocp = (c == 0 ? NCT - 1 : c - 1) - LAGT;
                     if (ocp >= 0 && ocp < NOBT && (c > 0 || k > 0)) {
                         if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
                         ph2 ^= 1;
                         fence_after();
-                        stage_C(ocp, 16 * ocp + 8 * e);
+                        stage_C(ocp, (c == 0 ? tbase(k - 1) : tb) + 16 * ocp + 8 * e);
                     }
                     if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
                     ph1 ^= 1;
                     fence_after();
-                    stage_X(16 * (c % (LAGT + 1)));
+                    if constexpr (kRingConst) {
+                        stage_X(16 * (c % (LAGT + 1)));
+                    } else {
+                        stage_X(krS);
+                        krS += 16;
+                        if (krS == 16 * (LAGT + 1)) krS = 0;
+                    }
                     if (!step_done()) goto cmp_tile_end;
                 }
             }
@@ -656,7 +686,7 @@ __global__ void __launch_bounds__(kT, 1)
                 if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
                 ph2 ^= 1;
                 fence_after();
-                stage_C(NCT - 1 - LAGT, 16 * (NCT - 1 - LAGT) + 8 * e);
+                stage_C(NCT - 1 - LAGT, tbase(K - 1) + 16 * (NCT - 1 - LAGT) + 8 * e);
             }
         } else {
             // ---- pipeline ----------------------------------------------------------------------
@@ -846,14 +876,19 @@ void tc_fit_waves(TcImg &g) {
 }
 
 // Tile offsets and the shared-memory layout of an ordered table.  When every
-// image has the geometry of the specialised kernel (r = 17..24 with 80-row
-// tiles: 8 chunks per term, lag 3), its centre ring takes 128 rows.
+// image has one of the geometries in kSpecGeom, the specialised kernel runs and
+// the centre ring takes 16 nc rows.
 void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
-    bool spec = true;
-    for (int i = 0; i < m; ++i) spec = spec && tab[i].nc == 8 && tab[i].lag == 3 && tab[i].BY == 80;
+    int spec = 0;
+    for (int j = 0; j < kNumSpec && !spec; ++j) {
+        bool all = m > 0;
+        for (int i = 0; i < m; ++i)
+            all = all && tab[i].nc == kSpecGeom[j].nc && tab[i].lag == kSpecGeom[j].lag && tab[i].BY == kSpecGeom[j].BY;
+        if (all) spec = j + 1;
+    }
     int max_ringA = 16, max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16, t = 0;
     for (int i = 0; i < m; ++i) {
-        if (spec) tab[i].ringC = 128;
+        if (spec) tab[i].ringC = 16 * tab[i].nc * kSpecGeom[spec - 1].terms;
         max_ringA = std::max(max_ringA, tab[i].ringA);
         tab[i].tile_begin = t;
         t += tab[i].tiles_x * cdiv(tab[i].H, tab[i].BY);
@@ -864,7 +899,7 @@ void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
     }
     *total = t;
     *lay = tc_layout(max_ringA, max_Kw, max_Kw1, max_ringC, max_BY);
-    lay->spec = spec ? 1 : 0;
+    lay->spec = spec;
 }
 
 // Launch over a table already in device memory.  The table is ordered by
@@ -876,11 +911,17 @@ int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *statu
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if ((int)lay.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
-    void (*kern)(const TcImg *, int, int, int *, int *, TcLayout);
-    if (lay.spec)
-        kern = variant == BF_BF16TC ? mcsf_tc_kernel<true, 8, 3, 5> : mcsf_tc_kernel<false, 8, 3, 5>;
-    else
-        kern = variant == BF_BF16TC ? mcsf_tc_kernel<true, 0, 0, 0> : mcsf_tc_kernel<false, 0, 0, 0>;
+    using Kern = void (*)(const TcImg *, int, int, int *, int *, TcLayout);
+    static constexpr Kern kFp16[kNumSpec + 1] = {
+        mcsf_tc_kernel<false, 0, 0, 0, 1>, mcsf_tc_kernel<false, 6, 1, 5, 1>, mcsf_tc_kernel<false, 7, 2, 5, 1>,
+        mcsf_tc_kernel<false, 8, 3, 5, 1>, mcsf_tc_kernel<false, 3, 1, 2, 2>, mcsf_tc_kernel<false, 4, 2, 2, 2>,
+        mcsf_tc_kernel<false, 6, 2, 4, 1>};
+    static constexpr Kern kBf16[kNumSpec + 1] = {
+        mcsf_tc_kernel<true, 0, 0, 0, 1>, mcsf_tc_kernel<true, 6, 1, 5, 1>, mcsf_tc_kernel<true, 7, 2, 5, 1>,
+        mcsf_tc_kernel<true, 8, 3, 5, 1>, mcsf_tc_kernel<true, 3, 1, 2, 2>, mcsf_tc_kernel<true, 4, 2, 2, 2>,
+        mcsf_tc_kernel<true, 6, 2, 4, 1>};
+    if (lay.spec < 0 || lay.spec > kNumSpec) return BF_ERR_ARG;
+    const Kern kern = variant == BF_BF16TC ? kBf16[lay.spec] : kFp16[lay.spec];
     // The register split inside the kernel assumes the launch gives each thread
     // kRegsLaunch registers; with fewer the compute warps' request could not be met.
     cudaFuncAttributes fa{};

@@ -381,6 +381,59 @@ def test_tc_batch_equals_single_calls_and_oracle(bf, variant):
         _check_tc(got, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
 
 
+@pytest.mark.parametrize("s", [1.0, 4.0, 8.0, 10.0])
+def test_tc_specialised_geometries(bf, s):
+    """A batch keeps the default tile of its window (one image alone may take a
+    shorter one), so two images of one sigma_s run the step loop specialised to
+    that geometry (r = 3, 12, 24: lag 1 to 3; r = 30 runs the general loop).
+    Each result equals the one of filtering the image alone (which runs the
+    general loop on these small images) and stays within the tensor-core
+    tolerance of the oracle."""
+    items, outs, keep, singles, refs = [], [], [], [], []
+    for i, (H, W) in enumerate([(170, 150), (96, 200)]):
+        C = synth.spd_cond(3, seed=800 + i)
+        f = synth.voronoi_image(H, W, 3, 7, 10.0, seed=810 + i)
+        plan = bf.bf_plan(3, C, s, 10, 32, 90 + i)
+        x = bf.to_pitched(f)
+        y = bf.pitched_empty(3, H, W)
+        items.append((plan, x.data_ptr(), y.data_ptr(), H, W, x.stride(1)))
+        outs.append(y)
+        keep.append((x, plan))
+        singles.append(_run(bf, plan, f, bf.BF_FP16TC))
+        refs.append((f, C, 90 + i))
+    bf.bf_filter_batch(items, bf.BF_FP16TC, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert bf.bf_last_status(0) == bf.BF_OK
+    for y, single, (f, C, seed) in zip(outs, singles, refs):
+        got = y.cpu().numpy().astype(np.float64)
+        assert np.array_equal(got, single)
+        ref, res = _oracle_full(f, s, C, 10, 32, seed)
+        _check_tc(got, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
+
+
+@pytest.mark.parametrize("s", [1.0, 4.0])
+def test_tc_two_term_ring_geometries(bf, s):
+    """A 512x512 image alone takes 32-row tiles (one wave of 128 tiles), which
+    run the step loop with a two-term centre ring (r = 3: 3 chunks per term,
+    lag 1; r = 12: 4 chunks, lag 2); in a batch of two the same image takes
+    80-row tiles (one-term ring).  Both results are identical and within the
+    tensor-core tolerance of the oracle."""
+    C = synth.spd_cond(3, seed=820)
+    f = synth.voronoi_image(512, 512, 3, 9, 10.0, seed=821)
+    plan = bf.bf_plan(3, C, s, 10, 32, 95)
+    alone = _run(bf, plan, f, bf.BF_FP16TC)
+    x = bf.to_pitched(f)
+    ys = [bf.pitched_empty(3, 512, 512) for _ in range(2)]
+    items = [(plan, x.data_ptr(), y.data_ptr(), 512, 512, x.stride(1)) for y in ys]
+    bf.bf_filter_batch(items, bf.BF_FP16TC, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert bf.bf_last_status(0) == bf.BF_OK
+    for y in ys:
+        assert np.array_equal(y.cpu().numpy().astype(np.float64), alone)
+    ref, res = _oracle_full(f, s, C, 10, 32, 95)
+    _check_tc(alone, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
+
+
 def test_host_async_equals_host_entry_point(bf):
     """bf_filter_host_async on two streams gives the results of bf_filter_host."""
     w = synth.WORKLOADS["small"]()
