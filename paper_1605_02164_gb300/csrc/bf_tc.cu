@@ -7,19 +7,19 @@
 // plus an r-pixel halo, at most 128 x 128 pixels) stays resident in tensor
 // memory as FP32 for all K terms.  For each term the region is streamed in
 // chunks of 16 rows:
-//   A  (all threads) phase theta = 2 pi nu.f in FP32 radians, SFU cos/sin,
+//   A  (compute warps) phase theta = 2 pi nu.f in FP32 radians, SFU cos/sin,
 //      and the 8 modulated channels cos f_c, cos, sin f_c, sin of 16 rows x
 //      128 columns, stored as FP16/BF16 in the K-major operand layout
 //      (M = 16 rows x 8 channels = 128, K = columns);
-//   M1 (one thread) horizontal pass, one chain of m128n64k16 MMAs:
+//   M1 (one issuer thread) horizontal pass, one chain of m128n64k16 MMAs:
 //      D1[128 x 64] = A1[128 x Kw1] * T1[Kw1 x 64], T1 the Toeplitz band of
 //      the normalised 1-D taps (Kw1 = 16 ceil((64 + 2r) / 16));
-//   X  (all threads) D1 (TMEM) -> FP16/BF16 into a ring of horizontally
+//   X  (compute warps) D1 (TMEM) -> FP16/BF16 into a ring of horizontally
 //      blurred rows, laid out MN-major (M = 64 columns x 8 channels);
-//   M2 (4 threads) vertical pass for the 16 output rows that became
+//   M2 (4 issuer threads) vertical pass for the 16 output rows that became
 //      complete: 4 M-tiles D2[128 x 16] = A2[128 x Kw] * T2[Kw x 16]
 //      (Kw = 16 + 16 ceil(2r / 16));
-//   C  (all threads) combine with the centre pixel's cos/sin into
+//   C  (compute warps) combine with the centre pixel's cos/sin into
 //      register accumulators P_1..P_3, Z (FP32).
 // After the last term out_c = P_c / Z.  Every wait on the tensor core is
 // bounded: on timeout the CTA records BF_ERR_TIMEOUT in the status word,
