@@ -236,6 +236,22 @@ int bf_filter_host_async(bf_plan_t plan, const float *in_host, float *out_host, 
  * BF_OK or the first BF_ERR_* recorded, and clears it. */
 int bf_last_status(void *stream);
 
+/* Fault injection, for tests of the error paths (no fault, trap or hang is
+ * ever caused on the device).  Arms one-shot faults, OR-ed into those already
+ * armed (0 disarms all); each is consumed by the first call that reaches it:
+ *   BF_FAULT_ALLOC    the next request to the library's device allocators
+ *                     (plan creation, per-stream scratch) fails with
+ *                     BF_ERR_NOMEM, as if the device were out of memory;
+ *   BF_FAULT_TC_WAIT  the next tensor-core launch skips its first group of
+ *                     MMAs and uses a short spin limit, so the compute warps'
+ *                     bounded wait runs out: every CTA stops after its first
+ *                     tile, the output is not written, the launch's status
+ *                     word reads BF_ERR_TIMEOUT (bf_last_status).
+ * Returns BF_OK, or BF_ERR_ARG for an unknown bit.  Thread-safe. */
+#define BF_FAULT_ALLOC 1
+#define BF_FAULT_TC_WAIT 2
+int bf_debug_inject(int faults);
+
 /* Static description of an error code. */
 const char *bf_error_string(int code);
 

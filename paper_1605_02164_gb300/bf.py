@@ -28,6 +28,9 @@ BF_ERR_TIMEOUT = -7
 BF_ERR_CUDA = -8
 BF_ERR_UNSUPPORTED = -9
 
+BF_FAULT_ALLOC = 1      # bf_debug_inject: the next library allocation request fails
+BF_FAULT_TC_WAIT = 2    # bf_debug_inject: the next tensor-core launch's bounded wait runs out
+
 BF_MAX_D = 8
 BF_MAX_RADIUS = 32
 BF_MAX_PLAN_RADIUS = 4096
@@ -90,6 +93,7 @@ def _load():
         lib.bf_rgb_to_lab.argtypes = [vp, vp, i, i, i, vp]
         lib.bf_lab_to_rgb.argtypes = [vp, vp, i, i, i, vp]
         lib.bf_last_status.argtypes = [vp]
+        lib.bf_debug_inject.argtypes = [i]
         lib.bf_error_string.argtypes = [i]
         lib.bf_error_string.restype = ctypes.c_char_p
         lib.bf_version.restype = i
@@ -237,6 +241,11 @@ def bf_last_status(stream: int = 0) -> int:
 
 def bf_version() -> int:
     return int(_load().bf_version())
+
+
+def bf_debug_inject(faults: int) -> None:
+    """Arm one-shot faults for tests of the error paths (0 disarms)."""
+    _check(_load().bf_debug_inject(int(faults)), "bf_debug_inject")
 
 
 # ---------------------------------------------------------------------------

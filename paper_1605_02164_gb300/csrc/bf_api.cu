@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -31,6 +32,15 @@ int check_image_args(const bf_plan_s *p, const float *in, const float *out, int 
     return BF_OK;
 }
 
+std::atomic<int> g_faults{0};
+
+bool take_fault(int mask) {
+    int cur = g_faults.load();
+    while (cur & mask)
+        if (g_faults.compare_exchange_weak(cur, cur & ~mask)) return true;
+    return false;
+}
+
 void *stream_scratch(cudaStream_t stream, size_t bytes) {
     struct Slot {
         int device;
@@ -40,6 +50,7 @@ void *stream_scratch(cudaStream_t stream, size_t bytes) {
     };
     static std::mutex mu;
     static std::vector<Slot> slots;
+    if (take_fault(BF_FAULT_ALLOC)) return nullptr;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
     std::lock_guard<std::mutex> lk(mu);
@@ -307,6 +318,15 @@ extern "C" int bf_last_status(void *stream) {
     if (v != 0) cudaMemset(w, 0, sizeof(int));
     const int v2 = bf::noalloc_take_status();  // the allocation-free entry point keeps its own word
     return v != 0 ? v : v2;
+}
+
+extern "C" int bf_debug_inject(int faults) {
+    if (faults & ~(BF_FAULT_ALLOC | BF_FAULT_TC_WAIT)) return BF_ERR_ARG;
+    if (faults == 0)
+        bf::g_faults.store(0);
+    else
+        bf::g_faults.fetch_or(faults);
+    return BF_OK;
 }
 
 extern "C" const char *bf_error_string(int code) {

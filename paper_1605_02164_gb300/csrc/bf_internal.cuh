@@ -36,6 +36,8 @@ constexpr uint32_t kPlanMagic = 0xBF1605u;
 
 // Status word: one per device, written by device guards, read by bf_last_status.
 int *status_word(int device);
+// Consumes the armed one-shot fault(s) in `mask` (bf_debug_inject); true if one was armed.
+bool take_fault(int mask);
 // Status word of bf_filter_batch_noalloc on the current device (cleared when read).
 int noalloc_take_status();
 

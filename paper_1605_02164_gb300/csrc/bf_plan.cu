@@ -251,6 +251,7 @@ int make_plan(int d, const double *C, double sigma_s, int N, int K, uint64_t see
     int r = radius >= 0 ? radius : (int)floor(3.0 * sigma_s + 1e-9);
     if (r > BF_MAX_PLAN_RADIUS) return BF_ERR_UNSUPPORTED;
 
+    if (take_fault(BF_FAULT_ALLOC)) return BF_ERR_NOMEM;
     bf_plan_s *p = new (std::nothrow) bf_plan_s;
     if (!p) return BF_ERR_NOMEM;
     p->d = d;

@@ -54,6 +54,7 @@ constexpr uint32_t kColD1 = 384;
 constexpr uint32_t kColD2 = 448;
 constexpr uint32_t kTmemCols = 512;
 constexpr int kSpinLimit = 1 << 22;
+constexpr int kInjectSpin = 1 << 12;  // spin limit of a launch with BF_FAULT_TC_WAIT armed
 // Centre ring: float2 (cos, sin) per output column; ring row t holds flat output
 // row t mod ringC, ringC = 16 (lag + 3) (flat output row = flat region row - r).
 // Column c of ring row t is stored at t * kBX + (c ^ ring_xor(t)): whatever r,
@@ -81,7 +82,9 @@ static_assert(sizeof(TcImg) == 96, "descriptor layout");
 // Shared-memory layout of a launch, sized for the largest window in it.
 struct TcLayout {
     uint32_t offA2, offB1, offB, offC, smem;
-    int spec;  // index + 1 into kSpecGeom when every image has that geometry, else 0
+    int spec;    // index + 1 into kSpecGeom when every image has that geometry, else 0
+    int spin;    // try_wait attempts before a wait on the tensor core gives up
+    int inject;  // 1: skip the first MMA group of every tile (BF_FAULT_TC_WAIT), so the wait runs out
 };
 
 // Geometries with a specialised step loop: the default tile of the lag classes
@@ -130,9 +133,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit) {
     const uint32_t a = smem_u32(bar);
-    for (int i = 0; i < kSpinLimit; ++i) {
+    for (int i = 0; i < limit; ++i) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -370,7 +373,7 @@ __global__ void __launch_bounds__(kT, 1)
                 iss_stop = true;
                 goto iss_tile_end;
             }
-            if (t == 0 && l == 0) {
+            if (t == 0 && l == 0 && !lay.inject) {
                 fence_after();
                 issue_M1(0);
             }
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(kT, 1)
             if (w == kComputeWarps) atomicCAS(status, 0, BF_ERR_TIMEOUT);
             // drain: bounded wait for every MMA this thread issued (a barrier of its own, fresh phase)
             mma_commit(&mbar[2 + (w - kComputeWarps)]);
-            mbar_wait(&mbar[2 + (w - kComputeWarps)], 0);
+            mbar_wait(&mbar[2 + (w - kComputeWarps)], 0, lay.spin);
         }
         fence_before();
         __syncthreads();  // final
@@ -664,12 +667,12 @@ __global__ void __launch_bounds__(kT, 1)
                     // output chunk completed by the previous step (of term k - 1 when c = 0)
                     const int ocp = (c == 0 ? NCT - 1 : c - 1) - LAGT;
                     if (ocp >= 0 && ocp < NOBT && (c > 0 || k > 0)) {
-                        if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                        if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                         ph2 ^= 1;
                         fence_after();
                         stage_C(ocp, (c == 0 ? tbase(k - 1) : tb) + 16 * ocp + 8 * e);
                     }
-                    if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
+                    if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
                     ph1 ^= 1;
                     fence_after();
                     if constexpr (kRingConst) {
@@ -683,7 +686,7 @@ __global__ void __launch_bounds__(kT, 1)
                 }
             }
             if (NCT - 1 - LAGT >= 0 && NCT - 1 - LAGT < NOBT) {
-                if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                 ph2 ^= 1;
                 fence_after();
                 stage_C(NCT - 1 - LAGT, tbase(K - 1) + 16 * (NCT - 1 - LAGT) + 8 * e);
@@ -706,13 +709,13 @@ __global__ void __launch_bounds__(kT, 1)
                     if (slotA >= g.ringC) slotA -= g.ringC;
                     if (s + 1 < S) stage_A(s + 1, cA, slotA);
                     if (pend_oc >= 0) {
-                        if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                        if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                         ph2 ^= 1;
                         fence_after();
                         stage_C(pend_oc, pend_slot);
                         pend_oc = -1;
                     }
-                    if (!mbar_wait(&mbar[0], ph1)) timed_out = true;
+                    if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
                     ph1 ^= 1;
                     fence_after();
                     stage_X(krS);
@@ -732,7 +735,7 @@ __global__ void __launch_bounds__(kT, 1)
                 }
             }
             if (pend_oc >= 0) {
-                if (!mbar_wait(&mbar[1], ph2)) timed_out = true;
+                if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                 ph2 ^= 1;
                 fence_after();
                 stage_C(pend_oc, pend_slot);
@@ -818,6 +821,8 @@ TcLayout tc_layout(int max_ringA, int max_Kw, int max_Kw1, int max_ringC, int ma
     const uint32_t z_bytes = (uint32_t)max_BY * kBX * 4;
     L.smem = L.offC + (ring_bytes > z_bytes ? ring_bytes : z_bytes);
     if (L.smem < 120 * 1024) L.smem = 120 * 1024;  // one CTA per SM: it holds all 512 TMEM columns
+    L.spin = kSpinLimit;
+    L.inject = 0;
     return L;
 }
 
@@ -904,8 +909,13 @@ void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
 
 // Launch over a table already in device memory.  The table is ordered by
 // per-tile cost (largest first) so the dynamic queue ends on cheap tiles.
-int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *status_dev, const TcLayout &lay,
+int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *status_dev, const TcLayout &lay_in,
               int variant, cudaStream_t s) {
+    TcLayout lay = lay_in;
+    if (take_fault(BF_FAULT_TC_WAIT)) {
+        lay.inject = 1;
+        lay.spin = kInjectSpin;
+    }
     int dev = 0, max_smem = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

@@ -18,7 +18,8 @@ time.  The server
     requests that arrive while others are on the GPU join the next batch and
     their work overlaps the batches already running (continuous batching);
   * completes requests as their batch's event fires, frees their budget and
-    records per-request latency (arrival to completion).
+    records per-request latency (arrival to completion);
+  * lets a caller withdraw a request that is still queued (cancel).
 Every filtering step runs in libbf's kernels; this module only schedules.
 """
 from __future__ import annotations
@@ -33,7 +34,9 @@ import numpy as np
 
 from . import bf
 
-__all__ = ["Request", "Server", "summarize"]
+__all__ = ["Request", "Server", "summarize", "CANCELLED"]
+
+CANCELLED = -100  # status of a request withdrawn by Server.cancel before admission
 
 
 @dataclass
@@ -54,7 +57,7 @@ class Request:
     out: object = None
     t_admit: float = math.nan
     t_done: float = math.nan
-    status: int = 1  # 1 pending, 0 done, < 0 BF_ERR_*
+    status: int = 1  # 1 pending, 0 done, < 0 BF_ERR_* or CANCELLED
     _bytes: int = 0
     done_evt: threading.Event = field(default_factory=threading.Event)
 
@@ -84,6 +87,7 @@ class Server:
         self.closed = False
         self.completed: list[Request] = []
         self.rejected: list[Request] = []
+        self.cancelled: list[Request] = []
         self.batches = 0
         self._thread = None
 
@@ -129,6 +133,21 @@ class Server:
             self.queue.append(req)
             self.cv.notify()
         return req
+
+    def cancel(self, req: Request) -> bool:
+        """Withdraw a request that is still queued (not yet admitted): it is
+        completed with status CANCELLED and no output.  Returns False when the
+        request was already admitted (its batch runs to the end) or finished."""
+        with self.cv:
+            try:
+                self.queue.remove(req)
+            except ValueError:
+                return False
+            req.status = CANCELLED
+            req.t_done = time.perf_counter()
+            self.cancelled.append(req)
+            req.done_evt.set()
+            return True
 
     def start(self):
         self._thread = threading.Thread(target=self._loop, name="bf-serve", daemon=True)
@@ -233,7 +252,8 @@ def summarize(reqs: list[Request], t0: float, t1: float) -> dict:
     px = sum(r.x.shape[1] * r.x.shape[2] for r in done)
     span = max(t1 - t0, 1e-9)
     return {"completed": len(done), "rejected": sum(1 for r in reqs if r.status == bf.BF_ERR_BUDGET),
-            "failed": sum(1 for r in reqs if r.status < 0 and r.status != bf.BF_ERR_BUDGET),
+            "cancelled": sum(1 for r in reqs if r.status == CANCELLED),
+            "failed": sum(1 for r in reqs if r.status < 0 and r.status not in (bf.BF_ERR_BUDGET, CANCELLED)),
             "images_per_s": len(done) / span, "mpixel_per_s": px / span / 1e6,
             "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
             "span_s": span}

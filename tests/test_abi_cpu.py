@@ -92,3 +92,22 @@ def test_host_entry_points_argument_checks(lib):
         assert fn(vp(1), buf, buf, -1, 4, 0, None) == bf.BF_ERR_ARG        # negative size
         assert fn(vp(1), None, buf, 4, 4, 0, None) == bf.BF_ERR_ARG        # null host buffer
         assert fn(vp(1), buf, buf, 0, 4, 0, None) == bf.BF_OK              # empty image: no-op
+
+
+def test_fault_injection_host_side(lib):
+    """bf_debug_inject: unknown bits are rejected; an armed allocation fault is
+    consumed by the next plan creation (after its argument checks), which
+    fails with BF_ERR_NOMEM before touching the device."""
+    from paper_1605_02164_gb300 import bf
+    L = bf.lib()
+    assert L.bf_debug_inject(4) == bf.BF_ERR_ARG
+    assert L.bf_debug_inject(-1) == bf.BF_ERR_ARG
+    C = (ctypes.c_double * 1)(900.0)
+    h = ctypes.c_void_p()
+    try:
+        assert L.bf_debug_inject(bf.BF_FAULT_ALLOC) == bf.BF_OK
+        assert L.bf_plan(1, C, -1.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_ARG  # checks first, fault kept
+        assert L.bf_plan(1, C, 2.0, 10, 8, 1, ctypes.byref(h)) == bf.BF_ERR_NOMEM
+        assert not h.value
+    finally:
+        assert L.bf_debug_inject(0) == bf.BF_OK

@@ -10,6 +10,7 @@ Pixels whose oracle Re Z falls below 1e-2 of the window's spatial weight sum
 are excluded from max-abs (near-zero normaliser; none occur on these inputs,
 and the count is asserted to be 0)."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -432,6 +433,70 @@ def test_tc_two_term_ring_geometries(bf, s):
         assert np.array_equal(y.cpu().numpy().astype(np.float64), alone)
     ref, res = _oracle_full(f, s, C, 10, 32, 95)
     _check_tc(alone, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
+
+
+@pytest.mark.parametrize("batch", [False, True])
+def test_tc_bounded_wait_reports_timeout(bf, batch):
+    """An injected fault (bf_debug_inject(BF_FAULT_TC_WAIT)) makes the
+    tensor-core kernel skip its first MMA group, so the compute warps' bounded
+    wait runs out: the launch ends (no hang), its status reads BF_ERR_TIMEOUT,
+    and the next call on the same stream is correct again with status BF_OK.
+    Alone, this image runs the general step loop; a batch of two runs the
+    specialised one (r = 9, 80-row tiles)."""
+    w = synth.WORKLOADS["small"]()
+    f = w.image()[:, :120, :150].copy()
+    plan = bf.bf_plan(w.d, w.C, w.sigma_s, w.N, 8, 31)
+    x = bf.to_pitched(f)
+    ys = [bf.pitched_empty(3, 120, 150) for _ in range(2 if batch else 1)]
+
+    def launch():
+        items = [(plan, x.data_ptr(), y.data_ptr(), 120, 150, x.stride(1)) for y in ys]
+        bf.bf_filter_batch(items, bf.BF_FP16TC, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        return [y.cpu().numpy() for y in ys]
+
+    good = launch()
+    assert bf.bf_last_status(0) == bf.BF_OK
+    bf.bf_debug_inject(bf.BF_FAULT_TC_WAIT)
+    try:
+        t0 = time.perf_counter()
+        launch()
+        assert bf.bf_last_status(0) == bf.BF_ERR_TIMEOUT
+        assert time.perf_counter() - t0 < 60.0
+    finally:
+        bf.bf_debug_inject(0)
+    again = launch()
+    assert all(np.array_equal(a, b) for a, b in zip(again, good))
+    assert bf.bf_last_status(0) == bf.BF_OK
+
+
+def test_allocation_fault_is_reported_and_recovered(bf):
+    """An injected allocation fault (BF_FAULT_ALLOC) fails the next request to
+    the library's allocators with BF_ERR_NOMEM (here: a filter on a new stream,
+    which needs scratch); the fault is one-shot and the retry succeeds."""
+    w = synth.WORKLOADS["small"]()
+    f = w.image()[:, :64, :96].copy()
+    plan = bf.bf_plan(w.d, w.C, w.sigma_s, w.N, 8, 32)
+    good = _run(bf, plan, f, bf.BF_FP16TC)
+    x = bf.to_pitched(f)
+    s = torch.cuda.Stream()
+    bf.bf_debug_inject(bf.BF_FAULT_ALLOC)
+    try:
+        with pytest.raises(bf.BFError) as e:
+            bf.filter_tensor(plan, x, bf.BF_FP16TC, stream=s)
+        assert e.value.code == bf.BF_ERR_NOMEM
+    finally:
+        bf.bf_debug_inject(0)
+    with torch.cuda.stream(s):
+        y = bf.filter_tensor(plan, x, bf.BF_FP16TC, stream=s)
+    s.synchronize()
+    assert np.array_equal(y.cpu().numpy().astype(np.float64), good)
+    with pytest.raises(bf.BFError) as e:  # plan creation: the same one-shot fault
+        bf.bf_debug_inject(bf.BF_FAULT_ALLOC)
+        bf.bf_plan(w.d, w.C, w.sigma_s, w.N, 8, 33)
+    assert e.value.code == bf.BF_ERR_NOMEM
+    bf.bf_debug_inject(0)
+    assert bf.bf_plan(w.d, w.C, w.sigma_s, w.N, 8, 33).K == 8
 
 
 def test_host_async_equals_host_entry_point(bf):

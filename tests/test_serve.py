@@ -118,3 +118,30 @@ def test_wide_window_rejected_alone_and_recursive_request_served(bf):
     torch.cuda.synchronize()
     assert torch.equal(alone, wide_rec.out)
     assert srv.used == 0
+
+
+def test_cancelled_request_is_not_run(bf):
+    """A request withdrawn while still queued completes with CANCELLED, no
+    output and no budget held; cancelling an admitted or finished request is
+    refused; the other requests are served and equal lone calls."""
+    from paper_1605_02164_gb300.serve import CANCELLED, Server, summarize
+    reqs = _requests(bf, 5, seed=21)
+    srv = Server(budget_bytes=64 << 20, streams=2, max_batch=8)  # not started: everything stays queued
+    for r in reqs:
+        srv.submit(r)
+    victim = reqs[2]
+    assert srv.cancel(victim)
+    assert victim.status == CANCELLED and victim.done_evt.is_set() and victim.out is None
+    assert not srv.cancel(victim)
+    t0 = time.perf_counter()
+    srv.start()
+    rest = [r for r in reqs if r is not victim]
+    for r in rest:
+        assert r.done_evt.wait(120)
+    assert not srv.cancel(rest[0])  # finished
+    srv.close()
+    s = summarize(reqs, t0, time.perf_counter())
+    assert s["completed"] == len(rest) and s["cancelled"] == 1 and s["failed"] == 0
+    assert srv.used == 0 and srv.cancelled == [victim]
+    for r in rest:
+        assert np.array_equal(r.out.cpu().numpy(), _alone(bf, r, bf.BF_FP16TC)), r.rid
