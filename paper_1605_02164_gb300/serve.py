@@ -139,9 +139,11 @@ class Server:
         completed with status CANCELLED and no output.  Returns False when the
         request was already admitted (its batch runs to the end) or finished."""
         with self.cv:
-            try:
-                self.queue.remove(req)
-            except ValueError:
+            for i, q in enumerate(self.queue):  # by identity (requests hold tensors)
+                if q is req:
+                    del self.queue[i]
+                    break
+            else:
                 return False
             req.status = CANCELLED
             req.t_done = time.perf_counter()
