@@ -382,8 +382,9 @@ def test_tc_batch_equals_single_calls_and_oracle(bf, variant):
         _check_tc(got, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
 
 
+@pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
 @pytest.mark.parametrize("s", [1.0, 4.0, 8.0, 10.0])
-def test_tc_specialised_geometries(bf, s):
+def test_tc_specialised_geometries(bf, s, variant):
     """A batch keeps the default tile of its window (one image alone may take a
     shorter one), so two images of one sigma_s run the step loop specialised to
     that geometry (r = 3, 12, 24: lag 1 to 3; r = 30 runs the general loop).
@@ -400,9 +401,9 @@ def test_tc_specialised_geometries(bf, s):
         items.append((plan, x.data_ptr(), y.data_ptr(), H, W, x.stride(1)))
         outs.append(y)
         keep.append((x, plan))
-        singles.append(_run(bf, plan, f, bf.BF_FP16TC))
+        singles.append(_run(bf, plan, f, bf.VARIANTS[variant]))
         refs.append((f, C, 90 + i))
-    bf.bf_filter_batch(items, bf.BF_FP16TC, torch.cuda.current_stream().cuda_stream)
+    bf.bf_filter_batch(items, bf.VARIANTS[variant], torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert bf.bf_last_status(0) == bf.BF_OK
     for y, single, (f, C, seed) in zip(outs, singles, refs):
@@ -412,8 +413,9 @@ def test_tc_specialised_geometries(bf, s):
         _check_tc(got, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
 
 
+@pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
 @pytest.mark.parametrize("s", [1.0, 4.0])
-def test_tc_two_term_ring_geometries(bf, s):
+def test_tc_two_term_ring_geometries(bf, s, variant):
     """A 512x512 image alone takes 32-row tiles (one wave of 128 tiles), which
     run the step loop with a two-term centre ring (r = 3: 3 chunks per term,
     lag 1; r = 12: 4 chunks, lag 2); in a batch of two the same image takes
@@ -422,11 +424,11 @@ def test_tc_two_term_ring_geometries(bf, s):
     C = synth.spd_cond(3, seed=820)
     f = synth.voronoi_image(512, 512, 3, 9, 10.0, seed=821)
     plan = bf.bf_plan(3, C, s, 10, 32, 95)
-    alone = _run(bf, plan, f, bf.BF_FP16TC)
+    alone = _run(bf, plan, f, bf.VARIANTS[variant])
     x = bf.to_pitched(f)
     ys = [bf.pitched_empty(3, 512, 512) for _ in range(2)]
     items = [(plan, x.data_ptr(), y.data_ptr(), 512, 512, x.stride(1)) for y in ys]
-    bf.bf_filter_batch(items, bf.BF_FP16TC, torch.cuda.current_stream().cuda_stream)
+    bf.bf_filter_batch(items, bf.VARIANTS[variant], torch.cuda.current_stream().cuda_stream)
     torch.cuda.synchronize()
     assert bf.bf_last_status(0) == bf.BF_OK
     for y in ys:
