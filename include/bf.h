@@ -52,6 +52,7 @@ extern "C" {
 #define BF_ERR_TIMEOUT (-7)     /* a bounded device-side wait ran out */
 #define BF_ERR_CUDA (-8)        /* a CUDA runtime call failed */
 #define BF_ERR_UNSUPPORTED (-9) /* parameters outside what the kernels handle */
+#define BF_ERR_BOUNDS (-10)     /* a device-side index check failed (checked build only) */
 
 #define BF_MAX_D 8        /* channels per pixel */
 #define BF_MAX_RADIUS 32  /* window half-width r of the windowed variants (sigma_s up to 10.99) */

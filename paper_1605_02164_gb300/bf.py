@@ -27,6 +27,7 @@ BF_ERR_BUDGET = -6
 BF_ERR_TIMEOUT = -7
 BF_ERR_CUDA = -8
 BF_ERR_UNSUPPORTED = -9
+BF_ERR_BOUNDS = -10
 
 BF_FAULT_ALLOC = 1      # bf_debug_inject: the next library allocation request fails
 BF_FAULT_TC_WAIT = 2    # bf_debug_inject: the next tensor-core launch's bounded wait runs out
@@ -64,7 +65,7 @@ class bf_item(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    return os.environ.get("BF_LIBRARY") or _build.LIB
 
 
 def _load():
@@ -72,7 +73,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = os.environ.get("BF_LIBRARY") or _build.LIB  # e.g. the checked build
         if not os.path.exists(path):
             raise ImportError(f"libbf is not built ({path} missing); run paper_1605_02164_gb300.build.build()")
         lib = ctypes.CDLL(path)

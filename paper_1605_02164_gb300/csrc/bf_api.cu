@@ -341,6 +341,7 @@ extern "C" const char *bf_error_string(int code) {
         case BF_ERR_TIMEOUT: return "bounded device wait ran out";
         case BF_ERR_CUDA: return "CUDA runtime error";
         case BF_ERR_UNSUPPORTED: return "parameters outside the supported range";
+        case BF_ERR_BOUNDS: return "device-side index check failed";
         default: return "unknown error";
     }
 }

@@ -166,6 +166,18 @@ __device__ __forceinline__ bool compute_sync_or(bool v) {
 __device__ __forceinline__ void step_arrive() { asm volatile("bar.arrive 2, %0;" ::"n"(kT) : "memory"); }
 __device__ __forceinline__ void step_wait() { asm volatile("bar.sync 2, %0;" ::"n"(kT) : "memory"); }
 
+// Index checks of the checked build (BF_DEVICE_CHECKS): a failed check records
+// BF_ERR_BOUNDS in the status word and the access it guards is skipped.  In the
+// normal build the check is the constant true and compiles away.
+#ifdef BF_DEVICE_CHECKS
+__device__ __forceinline__ bool dcheck(bool ok, int *status) {
+    if (!ok) atomicCAS(status, 0, BF_ERR_BOUNDS);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dcheck(bool, int *) { return true; }
+#endif
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -362,6 +374,7 @@ __global__ void __launch_bounds__(kT, 1)
                     if (ks < ksteps) {
                         int kg0 = kgb + 2 * ks;
                         if (kg0 >= kgring) kg0 -= kgring;
+                        if (!dcheck(kg0 >= 0 && kg0 + 2 <= kgring, status)) continue;
                         mma_f16(tmem + kColD2 + 16 * t, dA2 + (uint64_t)((kg0 * 8192 + t * 2048) >> 4),
                                 dB2 + 32 * ks, id2, ks > 0);
                     }
@@ -481,11 +494,14 @@ __global__ void __launch_bounds__(kT, 1)
             for (int ch = 0; ch < 3; ++ch) {
                 float v[4];
 #pragma unroll
-                for (int jj = 0; jj < 4; ++jj)
-                    v[jj] = ((vmask >> (4 * c + jj)) & 1)
-                                ? __ldg(in + ch * plane + (size_t)(ry0 + 16 * c + row) * pitch + (rx0 + 8 * xg + px0 + jj))
+                for (int jj = 0; jj < 4; ++jj) {
+                    const long long gy = ry0 + 16 * c + row, gx = rx0 + 8 * xg + px0 + jj;
+                    v[jj] = ((vmask >> (4 * c + jj)) & 1) && dcheck(gy >= 0 && gy < H && gx >= 0 && gx < W, status)
+                                ? __ldg(in + ch * plane + (size_t)gy * pitch + gx)
                                 : 0.f;
-                tmem_st4(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8 + pc0, v);
+                }
+                if (dcheck((2 * c + h) * 24 + ch * 8 + pc0 + 4 <= (int)kColD1, status))
+                    tmem_st4(tmem + lane_base + kColF + (2 * c + h) * 24 + ch * 8 + pc0, v);
             }
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -565,7 +581,8 @@ __global__ void __launch_bounds__(kT, 1)
                     o[6][p] = bits(__hmul2(hs, g2));
                 }
             }
-            if (centre_row) {  // centre cos/sin for the combine, ring row = flat output row mod ringC
+            if (centre_row && dcheck(slot16 + row - r >= -g.ringC && slot16 + row - r < g.ringC, status)) {
+                // centre cos/sin for the combine, ring row = flat output row mod ringC
                 int slot = slot16 + row - r;
                 if (slot < 0) slot += g.ringC;
                 float2 *rrow = ring + slot * kBX;
@@ -576,14 +593,17 @@ __global__ void __launch_bounds__(kT, 1)
             }
             // 4 pixels of one channel = half px0 / 4 of a 16-byte core-matrix row
             uint8_t *dst = dstA + (s & 1) * 32768;
+            if (dcheck(dst >= A1 && dst + 7 * 4096 + 8 <= A1 + 65536, status)) {
 #pragma unroll
-            for (int ch = 0; ch < 8; ++ch)
-                *reinterpret_cast<uint2 *>(dst + ch * 4096) = make_uint2(o[ch][0], o[ch][1]);
+                for (int ch = 0; ch < 8; ++ch)
+                    *reinterpret_cast<uint2 *>(dst + ch * 4096) = make_uint2(o[ch][0], o[ch][1]);
+            }
         };
 
         // C: combine output chunk oc; slot0 = ring row of its output row 16 oc + 8 e
         // (a multiple of 8 at most ringC - 8: the 8 rows read never wrap)
         auto stage_C = [&](int oc, int slot0) {
+            if (!dcheck(slot0 >= 0 && slot0 + 8 <= g.ringC && oc >= 0 && oc < NOC, status)) return;
             float vc[8], vs[8];  // output rows 16 oc + 8 e + j of the cos / sin M-tile
             tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h) + 8 * e, vc);
             tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h + 1) + 8 * e, vs);
@@ -611,6 +631,7 @@ __global__ void __launch_bounds__(kT, 1)
             const int kr = kr16 + row;
             uint8_t *base =
                 A2 + (size_t)(kr >> 3) * 8192 + (2 * h + gsel) * 2048 + (kr & 7) * 16 + p * 512 + 2 * e * 128;
+            if (!dcheck(kr >= 0 && kr < g.ringA, status)) return;
 #pragma unroll
             for (int i = 0; i < 2; ++i) {
                 const uint4 pk = make_uint4(bits(P2::make(v[8 * i], v[8 * i + 1])), bits(P2::make(v[8 * i + 2], v[8 * i + 3])),
@@ -755,7 +776,8 @@ __global__ void __launch_bounds__(kT, 1)
                 for (int o = 0; o < NOC; ++o)
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
-                        if (16 * o + 8 * e + j < BY) zbuf[(16 * o + 8 * e + j) * kBX + x] = acc[o][j];
+                        if (16 * o + 8 * e + j < BY && dcheck((16 * o + 8 * e + j + 1) * kBX * 4 <= (int)(lay.smem - lay.offC), status))
+                            zbuf[(16 * o + 8 * e + j) * kBX + x] = acc[o][j];
             }
             __syncthreads();  // z buffer
             const int gx = tx0 + x;
@@ -765,7 +787,7 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int y = 16 * o + 8 * e + j, gy = ty0 + y;
-                        if (y < BY && gy < H)
+                        if (y < BY && gy < H && dcheck(gy >= 0 && gx >= 0 && gx < W, status))
                             out[q * plane + (size_t)gy * pitch + gx] = acc[o][j] / zbuf[y * kBX + x];
                     }
             }
