@@ -169,7 +169,7 @@ int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
  * at start-up), where a foreign cudaMalloc can fail or fragment the pool, and
  * latency-critical loops that cannot absorb the device-wide synchronisation a
  * cudaMalloc or cudaFree may cause.  This entry point serves them: its
- * scratch is a file-scope device array of 24.25 KB (the control words plus
+ * scratch is a file-scope device array of 26.25 KB (the control words plus
  * the table for BF_NOALLOC_MAX_ITEMS images) that every GPU loading the
  * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
  * other allocating routine, on the device or the host.

@@ -31,6 +31,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "bf_internal.cuh"
@@ -63,6 +64,21 @@ constexpr int kInjectSpin = 1 << 12;  // spin limit of a launch with BF_FAULT_TC
 // A combine reads 8 rows starting at a multiple of 8, so its XORs are constants.
 __host__ __device__ constexpr int ring_xor(int t) { return (t & 3) | ((t & 4) << 1); }
 
+// Geometries with a specialised step loop in the kernel (the dispatch on
+// TcImg::spec lists the same values): the default tile of the lag classes
+// r = 1..8, 9..16 and 17..24; the 32-row tiles a 512 x 512 image takes alone at
+// r = 1..8 and 9..16 (two-term centre ring); the 64-row tile of a 1024 x 1024
+// image alone at r = 9..16.  (r = 25..32 keeps the general loop: a 128-row
+// centre ring would take the shared memory past 227 KB.)
+constexpr int kNumSpec = 6;
+struct SpecGeom {
+    int nc, lag, BY, terms;
+};
+constexpr SpecGeom kSpecGeom[kNumSpec] = {{6, 1, 80, 1}, {7, 2, 80, 1}, {8, 3, 80, 1},
+                                          {3, 1, 32, 2}, {4, 2, 32, 2}, {6, 2, 64, 1}};
+template <int V>
+using IC = std::integral_constant<int, V>;
+
 // One image of a launch (the single-image call is a batch of one).  The table
 // lives in device memory; tiles of all images form one work queue.
 struct TcImg {
@@ -75,29 +91,19 @@ struct TcImg {
     int Kw, ksteps;         // vertical pass: window rows 16 (lag + 1), K-steps of 16
     int Kw1, ks1;           // horizontal pass: 64 + 2r rounded up to 16, K-steps of 16
     int BY, nc, ringC;      // output rows per tile, 16-row chunks per term, centre-ring rows
-    int tiles_x, tile_begin, ringA;  // ringA: rows of the blurred-row ring (Kw, or Kw + 16)
+    int tiles_x, tile_begin, ringA;  // ringA: rows of the blurred-row ring
+    int spec, pad;                   // spec: index + 1 into kSpecGeom, or 0 (general loop)
 };
-static_assert(sizeof(TcImg) == 96, "descriptor layout");
+static_assert(sizeof(TcImg) == 104, "descriptor layout");
 
 // Shared-memory layout of a launch, sized for the largest window in it.
 struct TcLayout {
     uint32_t offA2, offB1, offB, offC, smem;
-    int spec;    // index + 1 into kSpecGeom when every image has that geometry, else 0
     int spin;    // try_wait attempts before a wait on the tensor core gives up
     int inject;  // 1: skip the first MMA group of every tile (BF_FAULT_TC_WAIT), so the wait runs out
 };
 
-// Geometries with a specialised step loop: the default tile of the lag classes
-// r = 1..8, 9..16 and 17..24; the 32-row tiles a 512 x 512 image takes alone at
-// r = 1..8 and 9..16 (two-term centre ring); the 64-row tile of a 1024 x 1024
-// image alone at r = 9..16.  (r = 25..32 keeps the general loop: a 128-row
-// centre ring would take the shared memory past 227 KB.)
-constexpr int kNumSpec = 6;
-struct SpecGeom {
-    int nc, lag, BY, terms;
-};
-constexpr SpecGeom kSpecGeom[kNumSpec] = {{6, 1, 80, 1}, {7, 2, 80, 1}, {8, 3, 80, 1},
-                                          {3, 1, 32, 2}, {4, 2, 32, 2}, {6, 2, 64, 1}};
+
 
 // Launch control words kept in device scratch: [0] tile counter (zeroed by
 // the copy that uploads the image table before every launch).
@@ -273,13 +279,7 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // warp 16).  Each MMA group runs while the compute warps do a step of work.
 // TMEM: region f 0..383, D1 384..447, D2 448..511 (single-buffered: each is
 // read back before the group that rewrites it is issued).
-// NCT > 0 specialises the compute warps' step loop to a geometry of NCT chunks
-// per term, lag LAGT and NOBT output chunks per tile, with the centre ring
-// 16 NCT PT rows long (PT terms): the chunk loop is unrolled and every ring
-// slot and output chunk of a step is a compile-time constant (plus a per-term
-// base when PT = 2).  NCT = 0 is the general loop (any geometry the tile
-// scheme holds).
-template <bool BF16, int NCT, int LAGT, int NOBT, int PT>
+template <bool BF16>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
                    int *__restrict__ status, TcLayout lay) {
@@ -659,109 +659,134 @@ __global__ void __launch_bounds__(kT, 1)
         stage_A(0, 0, 0);
         if (!step_done()) goto cmp_tile_end;
 
-        if constexpr (NCT > 0) {
-            // ---- pipeline, specialised geometry -----------------------------------------------
-            // Step (k, c): centre-ring slot tb(k) + 16 c, tb(k) = 16 NCT (k mod PT),
-            // output chunk c - LAGT; the A1 buffer (k NCT + c) & 1 and the
-            // blurred-row ring rows 16 ((k NCT + c) mod (LAGT + 1)) are constants
-            // too when NCT is even / a multiple of LAGT + 1, else they are carried
-            // from step to step.  The centre-ring rows a step writes (chunk c + 1,
-            // or chunk 0 of the next term) never meet the rows it combines (chunk
-            // c - 1 - LAGT, or the previous term's last): NCT >= LAGT + 3 keeps them
-            // apart in a one-term ring, PT = 2 puts consecutive terms in different halves.
-            static_assert((PT == 1 && NCT >= LAGT + 3) || (PT == 2 && NCT >= LAGT + 1), "geometry");
-            static_assert(NOBT <= NOC, "geometry");
-            constexpr bool kParConst = NCT % 2 == 0, kRingConst = NCT % (LAGT + 1) == 0;
-            auto tbase = [&](int kk) { return PT == 2 ? (kk & 1) * 16 * NCT : 0; };
-            int krS = 0;  // 16 s mod Kw when it is not a constant
-            for (int k = 0; k < K; ++k) {
-                const int kpar = kParConst ? 0 : (k & 1);
-                const int tb = tbase(k);
-#pragma unroll
-                for (int c = 0; c < NCT; ++c) {
-                    if (c + 1 < NCT) {
-                        stage_A(kpar + c + 1, c + 1, tb + 16 * (c + 1));
-                    } else if (k + 1 < K) {
-                        load_nu(k + 1);
-                        stage_A(kParConst ? 0 : (k + 1) & 1, 0, tbase(k + 1));
-                    }
-                    // output chunk completed by the previous step (of term k - 1 when c = 0)
-                    const int ocp = (c == 0 ? NCT - 1 : c - 1) - LAGT;
-                    if (ocp >= 0 && ocp < NOBT && (c > 0 || k > 0)) {
-                        if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
-                        ph2 ^= 1;
+        {
+            // Step loops.  A tile whose image has one of the geometries in
+            // kSpecGeom (g.spec = its index + 1) runs the loop specialised to it:
+            // chunks per term NCT, lag LAGT, NOBT output chunks, a centre ring of
+            // PT terms x 16 NCT rows; the chunk loop is unrolled and every ring slot
+            // and output chunk of a step is a compile-time constant.  Any other tile
+            // runs the general loop.  Both return false when the compute warps stop.
+            auto spec_loop = [&](auto nct_c, auto lag_c, auto nob_c, auto pt_c) -> bool {
+                constexpr int NCT = decltype(nct_c)::value, LAGT = decltype(lag_c)::value;
+                constexpr int NOBT = decltype(nob_c)::value, PT = decltype(pt_c)::value;
+                // ---- pipeline, specialised geometry -----------------------------------------------
+                // Step (k, c): centre-ring slot tb(k) + 16 c, tb(k) = 16 NCT (k mod PT),
+                // output chunk c - LAGT; the A1 buffer (k NCT + c) & 1 and the
+                // blurred-row ring rows 16 ((k NCT + c) mod (LAGT + 1)) are constants
+                // too when NCT is even / a multiple of LAGT + 1, else they are carried
+                // from step to step.  The centre-ring rows a step writes (chunk c + 1,
+                // or chunk 0 of the next term) never meet the rows it combines (chunk
+                // c - 1 - LAGT, or the previous term's last): NCT >= LAGT + 3 keeps them
+                // apart in a one-term ring, PT = 2 puts consecutive terms in different halves.
+                static_assert((PT == 1 && NCT >= LAGT + 3) || (PT == 2 && NCT >= LAGT + 1), "geometry");
+                static_assert(NOBT <= NOC, "geometry");
+                constexpr bool kParConst = NCT % 2 == 0, kRingConst = NCT % (LAGT + 1) == 0;
+                auto tbase = [&](int kk) { return PT == 2 ? (kk & 1) * 16 * NCT : 0; };
+                int krS = 0;  // 16 s mod Kw when it is not a constant
+                for (int k = 0; k < K; ++k) {
+                    const int kpar = kParConst ? 0 : (k & 1);
+                    const int tb = tbase(k);
+    #pragma unroll
+                    for (int c = 0; c < NCT; ++c) {
+                        if (c + 1 < NCT) {
+                            stage_A(kpar + c + 1, c + 1, tb + 16 * (c + 1));
+                        } else if (k + 1 < K) {
+                            load_nu(k + 1);
+                            stage_A(kParConst ? 0 : (k + 1) & 1, 0, tbase(k + 1));
+                        }
+                        // output chunk completed by the previous step (of term k - 1 when c = 0)
+                        const int ocp = (c == 0 ? NCT - 1 : c - 1) - LAGT;
+                        if (ocp >= 0 && ocp < NOBT && (c > 0 || k > 0)) {
+                            if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
+                            ph2 ^= 1;
+                            fence_after();
+                            stage_C(ocp, (c == 0 ? tbase(k - 1) : tb) + 16 * ocp + 8 * e);
+                        }
+                        if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
+                        ph1 ^= 1;
                         fence_after();
-                        stage_C(ocp, (c == 0 ? tbase(k - 1) : tb) + 16 * ocp + 8 * e);
+                        if constexpr (kRingConst) {
+                            stage_X(16 * (c % (LAGT + 1)));
+                        } else {
+                            stage_X(krS);
+                            krS += 16;
+                            if (krS == 16 * (LAGT + 1)) krS = 0;
+                        }
+                        if (!step_done()) return false;
                     }
-                    if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
-                    ph1 ^= 1;
+                }
+                if (NCT - 1 - LAGT >= 0 && NCT - 1 - LAGT < NOBT) {
+                    if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
+                    ph2 ^= 1;
                     fence_after();
-                    if constexpr (kRingConst) {
-                        stage_X(16 * (c % (LAGT + 1)));
-                    } else {
+                    stage_C(NCT - 1 - LAGT, tbase(K - 1) + 16 * (NCT - 1 - LAGT) + 8 * e);
+                }
+                return true;
+            };
+            auto general_loop = [&]() -> bool {
+                // ---- pipeline ----------------------------------------------------------------------
+                // Step s is chunk c of term k; slotS = 16 s mod ringC and krS = 16 s mod Kw
+                // are carried from step to step (no division in the loop), as are the
+                // chunk, term and slot of step s + 1 (cA, kA, slotA).
+                {
+                    int c = 0, kA = 0, cA = 0, slotS = 0, krS = 0;
+                    for (int s = 0; s < S; ++s) {
+                        const int oc = c - lag;
+                        const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
+                        if (++cA == NCr) {
+                            cA = 0;
+                            if (++kA < K) load_nu(kA);
+                        }
+                        int slotA = slotS + 16;
+                        if (slotA >= g.ringC) slotA -= g.ringC;
+                        if (s + 1 < S) stage_A(s + 1, cA, slotA);
+                        if (pend_oc >= 0) {
+                            if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
+                            ph2 ^= 1;
+                            fence_after();
+                            stage_C(pend_oc, pend_slot);
+                            pend_oc = -1;
+                        }
+                        if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
+                        ph1 ^= 1;
+                        fence_after();
                         stage_X(krS);
+                        if (!step_done()) return false;
+                        if (do_m2) {
+                            pend_oc = oc;
+                            // flat output row 16 (s - lag) + 8 e, mod ringC (16 lag < ringC)
+                            int sl = slotS - 16 * lag + 8 * e;
+                            if (sl < 0) sl += g.ringC;
+                            if (sl >= g.ringC) sl -= g.ringC;
+                            pend_slot = sl;
+                        }
+                        c = cA;
+                        slotS = slotA;
                         krS += 16;
-                        if (krS == 16 * (LAGT + 1)) krS = 0;
+                        if (krS == g.ringA) krS = 0;
                     }
-                    if (!step_done()) goto cmp_tile_end;
                 }
-            }
-            if (NCT - 1 - LAGT >= 0 && NCT - 1 - LAGT < NOBT) {
-                if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
-                ph2 ^= 1;
-                fence_after();
-                stage_C(NCT - 1 - LAGT, tbase(K - 1) + 16 * (NCT - 1 - LAGT) + 8 * e);
-            }
-        } else {
-            // ---- pipeline ----------------------------------------------------------------------
-            // Step s is chunk c of term k; slotS = 16 s mod ringC and krS = 16 s mod Kw
-            // are carried from step to step (no division in the loop), as are the
-            // chunk, term and slot of step s + 1 (cA, kA, slotA).
-            {
-                int c = 0, kA = 0, cA = 0, slotS = 0, krS = 0;
-                for (int s = 0; s < S; ++s) {
-                    const int oc = c - lag;
-                    const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
-                    if (++cA == NCr) {
-                        cA = 0;
-                        if (++kA < K) load_nu(kA);
-                    }
-                    int slotA = slotS + 16;
-                    if (slotA >= g.ringC) slotA -= g.ringC;
-                    if (s + 1 < S) stage_A(s + 1, cA, slotA);
-                    if (pend_oc >= 0) {
-                        if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
-                        ph2 ^= 1;
-                        fence_after();
-                        stage_C(pend_oc, pend_slot);
-                        pend_oc = -1;
-                    }
-                    if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
-                    ph1 ^= 1;
+                if (pend_oc >= 0) {
+                    if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
+                    ph2 ^= 1;
                     fence_after();
-                    stage_X(krS);
-                    if (!step_done()) goto cmp_tile_end;
-                    if (do_m2) {
-                        pend_oc = oc;
-                        // flat output row 16 (s - lag) + 8 e, mod ringC (16 lag < ringC)
-                        int sl = slotS - 16 * lag + 8 * e;
-                        if (sl < 0) sl += g.ringC;
-                        if (sl >= g.ringC) sl -= g.ringC;
-                        pend_slot = sl;
-                    }
-                    c = cA;
-                    slotS = slotA;
-                    krS += 16;
-                    if (krS == g.ringA) krS = 0;
+                    stage_C(pend_oc, pend_slot);
                 }
+                return true;
+            };
+            bool go;
+            switch (g.spec) {
+                case 1: go = spec_loop(IC<6>(), IC<1>(), IC<5>(), IC<1>()); break;
+                case 2: go = spec_loop(IC<7>(), IC<2>(), IC<5>(), IC<1>()); break;
+                case 3: go = spec_loop(IC<8>(), IC<3>(), IC<5>(), IC<1>()); break;
+                case 4: go = spec_loop(IC<3>(), IC<1>(), IC<2>(), IC<2>()); break;
+                case 5: go = spec_loop(IC<4>(), IC<2>(), IC<2>(), IC<2>()); break;
+                case 6: go = spec_loop(IC<6>(), IC<2>(), IC<4>(), IC<1>()); break;
+                default: go = general_loop(); break;
             }
-            if (pend_oc >= 0) {
-                if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
-                ph2 ^= 1;
-                fence_after();
-                stage_C(pend_oc, pend_slot);
-            }
+            if (!go) goto cmp_tile_end;
         }
+
         // ---- P / Z ----------------------------------------------------------------
         fence_before();
         if (__syncthreads_or(timed_out)) {  // tile barrier, with the issuers
@@ -902,31 +927,44 @@ void tc_fit_waves(TcImg &g) {
     g.nc = cdiv(g.BY + 2 * g.r, 16);
 }
 
-// Tile offsets and the shared-memory layout of an ordered table.  When every
-// image has one of the geometries in kSpecGeom, the specialised kernel runs and
-// the centre ring takes 16 nc rows.
+// Tile offsets, the step loop of each image (kSpecGeom) and the shared-memory
+// layout of an ordered table.  An image with a specialised loop has a centre
+// ring of 16 nc rows per term of that loop, if that ring fits in the shared
+// memory the rest of the launch's layout leaves (a batch that mixes in a wide
+// window may not leave it); otherwise it runs the general loop.
 void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
-    int spec = 0;
-    for (int j = 0; j < kNumSpec && !spec; ++j) {
-        bool all = m > 0;
-        for (int i = 0; i < m; ++i)
-            all = all && tab[i].nc == kSpecGeom[j].nc && tab[i].lag == kSpecGeom[j].lag && tab[i].BY == kSpecGeom[j].BY;
-        if (all) spec = j + 1;
-    }
     int max_ringA = 16, max_Kw = 16, max_Kw1 = 64, max_ringC = 48, max_BY = 16, t = 0;
     for (int i = 0; i < m; ++i) {
-        if (spec) tab[i].ringC = 16 * tab[i].nc * kSpecGeom[spec - 1].terms;
-        max_ringA = std::max(max_ringA, tab[i].ringA);
         tab[i].tile_begin = t;
         t += tab[i].tiles_x * cdiv(tab[i].H, tab[i].BY);
+        max_ringA = std::max(max_ringA, tab[i].ringA);
         max_Kw = std::max(max_Kw, tab[i].Kw);
         max_Kw1 = std::max(max_Kw1, tab[i].Kw1);
-        max_ringC = std::max(max_ringC, tab[i].ringC);
+        max_ringC = std::max(max_ringC, tab[i].ringC);  // the general loop's rings
         max_BY = std::max(max_BY, tab[i].BY);
+    }
+    int dev = 0, max_smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        max_smem = 0;  // no specialised rings
+    }
+    const TcLayout base = tc_layout(max_ringA, max_Kw, max_Kw1, 0, max_BY);
+    const long long ring_rows = ((long long)max_smem - 1024 - (long long)base.offC) / (kBX * 8);
+    for (int i = 0; i < m; ++i) {
+        tab[i].spec = 0;
+        for (int j = 0; j < kNumSpec; ++j) {
+            const int rows = 16 * kSpecGeom[j].nc * kSpecGeom[j].terms;
+            if (tab[i].nc == kSpecGeom[j].nc && tab[i].lag == kSpecGeom[j].lag && tab[i].BY == kSpecGeom[j].BY &&
+                rows <= ring_rows) {
+                tab[i].spec = j + 1;
+                tab[i].ringC = rows;
+            }
+        }
+        max_ringC = std::max(max_ringC, tab[i].ringC);
     }
     *total = t;
     *lay = tc_layout(max_ringA, max_Kw, max_Kw1, max_ringC, max_BY);
-    lay->spec = spec;
 }
 
 // Launch over a table already in device memory.  The table is ordered by
@@ -943,17 +981,7 @@ int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *statu
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if ((int)lay.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
-    using Kern = void (*)(const TcImg *, int, int, int *, int *, TcLayout);
-    static constexpr Kern kFp16[kNumSpec + 1] = {
-        mcsf_tc_kernel<false, 0, 0, 0, 1>, mcsf_tc_kernel<false, 6, 1, 5, 1>, mcsf_tc_kernel<false, 7, 2, 5, 1>,
-        mcsf_tc_kernel<false, 8, 3, 5, 1>, mcsf_tc_kernel<false, 3, 1, 2, 2>, mcsf_tc_kernel<false, 4, 2, 2, 2>,
-        mcsf_tc_kernel<false, 6, 2, 4, 1>};
-    static constexpr Kern kBf16[kNumSpec + 1] = {
-        mcsf_tc_kernel<true, 0, 0, 0, 1>, mcsf_tc_kernel<true, 6, 1, 5, 1>, mcsf_tc_kernel<true, 7, 2, 5, 1>,
-        mcsf_tc_kernel<true, 8, 3, 5, 1>, mcsf_tc_kernel<true, 3, 1, 2, 2>, mcsf_tc_kernel<true, 4, 2, 2, 2>,
-        mcsf_tc_kernel<true, 6, 2, 4, 1>};
-    if (lay.spec < 0 || lay.spec > kNumSpec) return BF_ERR_ARG;
-    const Kern kern = variant == BF_BF16TC ? kBf16[lay.spec] : kFp16[lay.spec];
+    auto kern = variant == BF_BF16TC ? mcsf_tc_kernel<true> : mcsf_tc_kernel<false>;
     // The register split inside the kernel assumes the launch gives each thread
     // kRegsLaunch registers; with fewer the compute warps' request could not be met.
     cudaFuncAttributes fa{};
@@ -1011,7 +1039,7 @@ int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int
 
 // Scratch of bf_filter_batch_noalloc: control words (tile counter, status)
 // followed by the image table for at most BF_NOALLOC_MAX_ITEMS images.  Every
-// GPU that loads the library holds these 24.25 KB until the process exits.
+// GPU that loads the library holds these 26.25 KB until the process exits.
 constexpr size_t kNoAllocBytes = (size_t)kCtrlWords * sizeof(int) + (size_t)BF_NOALLOC_MAX_ITEMS * sizeof(TcImg);
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
