@@ -99,6 +99,7 @@ static_assert(sizeof(TcImg) == 104, "descriptor layout");
 // Shared-memory layout of a launch, sized for the largest window in it.
 struct TcLayout {
     uint32_t offA2, offB1, offB, offC, smem;
+    int fix;     // the specialised loop every image of the launch runs (kSpecGeom index + 1), or 0
     int spin;    // try_wait attempts before a wait on the tensor core gives up
     int inject;  // 1: skip the first MMA group of every tile (BF_FAULT_TC_WAIT), so the wait runs out
 };
@@ -279,7 +280,13 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // warp 16).  Each MMA group runs while the compute warps do a step of work.
 // TMEM: region f 0..383, D1 384..447, D2 448..511 (single-buffered: each is
 // read back before the group that rewrites it is issued).
-template <bool BF16>
+// FIX = 0 chooses each tile's step loop from its image (TcImg::spec); FIX = j
+// compiles in only loop j, for a launch whose images all have that geometry.
+// Measured on the GB300s: the kernel with loop 4 or 5 alone (the
+// two-term rings of a 512 x 512 image) is 4 % faster than the dispatching one,
+// while for loops 1, 2, 3 and 6 the dispatching kernel is ~1 % faster (ptxas
+// arranges the two differently), so only FIX = 4 and 5 are built.
+template <bool BF16, int FIX>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
                    int *__restrict__ status, TcLayout lay) {
@@ -775,7 +782,7 @@ __global__ void __launch_bounds__(kT, 1)
                 return true;
             };
             bool go;
-            switch (g.spec) {
+            switch (FIX ? FIX : g.spec) {
                 case 1: go = spec_loop(IC<6>(), IC<1>(), IC<5>(), IC<1>()); break;
                 case 2: go = spec_loop(IC<7>(), IC<2>(), IC<5>(), IC<1>()); break;
                 case 3: go = spec_loop(IC<8>(), IC<3>(), IC<5>(), IC<1>()); break;
@@ -868,6 +875,7 @@ TcLayout tc_layout(int max_ringA, int max_Kw, int max_Kw1, int max_ringC, int ma
     const uint32_t z_bytes = (uint32_t)max_BY * kBX * 4;
     L.smem = L.offC + (ring_bytes > z_bytes ? ring_bytes : z_bytes);
     if (L.smem < 120 * 1024) L.smem = 120 * 1024;  // one CTA per SM: it holds all 512 TMEM columns
+    L.fix = 0;
     L.spin = kSpinLimit;
     L.inject = 0;
     return L;
@@ -965,6 +973,10 @@ void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
     }
     *total = t;
     *lay = tc_layout(max_ringA, max_Kw, max_Kw1, max_ringC, max_BY);
+    int fix = m > 0 ? tab[0].spec : 0;
+    for (int i = 1; i < m; ++i)
+        if (tab[i].spec != fix) fix = 0;
+    lay->fix = (fix == 4 || fix == 5) ? fix : 0;  // the kernels built with one loop (see FIX)
 }
 
 // Launch over a table already in device memory.  The table is ordered by
@@ -981,7 +993,15 @@ int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *statu
     cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if ((int)lay.smem + 1024 > max_smem) return BF_ERR_UNSUPPORTED;  // + the 1 KB-aligned static part
-    auto kern = variant == BF_BF16TC ? mcsf_tc_kernel<true> : mcsf_tc_kernel<false>;
+    using Kern = void (*)(const TcImg *, int, int, int *, int *, TcLayout);
+    Kern kern;
+    const bool b = variant == BF_BF16TC;
+    switch (lay.fix) {
+        case 0: kern = b ? mcsf_tc_kernel<true, 0> : mcsf_tc_kernel<false, 0>; break;
+        case 4: kern = b ? mcsf_tc_kernel<true, 4> : mcsf_tc_kernel<false, 4>; break;
+        case 5: kern = b ? mcsf_tc_kernel<true, 5> : mcsf_tc_kernel<false, 5>; break;
+        default: return BF_ERR_ARG;
+    }
     // The register split inside the kernel assumes the launch gives each thread
     // kRegsLaunch registers; with fewer the compute warps' request could not be met.
     cudaFuncAttributes fa{};
