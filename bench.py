@@ -45,7 +45,7 @@ def algorithmic_flops_per_pixel(d: int, r: int, K: int) -> float:
 # only stands for the kernel source it was taken on (sha1 of that file): after
 # any change to the source the bench reports null until a new capture.
 MEASURED_TRAFFIC = {
-    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "1a973e513e40c26870fecb3a3043610f4b1072e1",
+    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "72bbe6ac7b91740937590dcfe38310efcff2c38d",
                "workload": "4k", "bytes_per_launch": 100.601e6 + 58.787e6,
                "capture": "ncu --set full of one launch on this workload (profiles/mcsf_tc_4k_s8_K128.md)"},
     "fp32rec": {"src": "paper_1605_02164_gb300/csrc/bf_recursive.cu", "sha1": "ae50e6fedcb753639417caa1d0166d124187c5a9",

@@ -272,8 +272,7 @@ __device__ __forceinline__ uint32_t bits(T v) {
 //   1  build the channels of chunk s+1 (A) into the A1 buffer not being read,
 //   1b wait for the vertical MMAs issued after step s-1 and combine them (C),
 //   2  wait for the horizontal MMAs of chunk s and move D1 into the ring (X),
-//   3  meet at a compute-only barrier, after which one thread arrives on the
-//      step barrier;
+//   3  meet at a compute-only barrier and arrive on the step barrier;
 // then the issuer warps issue, when chunk s completes 16 output rows, the 4
 // vertical M-tiles (one chain of N = 16, K = 16 + 16 ceil(2r/16) per warp),
 // and the horizontal MMAs of chunk s+1 (one chain of N = 64, K = 64 + 2r,
@@ -282,10 +281,10 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // read back before the group that rewrites it is issued).
 // FIX = 0 chooses each tile's step loop from its image (TcImg::spec); FIX = j
 // compiles in only loop j, for a launch whose images all have that geometry.
-// Measured on the GB300s: the kernel with loop 4 or 5 alone (the
-// two-term rings of a 512 x 512 image) is 4 % faster than the dispatching one,
-// while for loops 1, 2, 3 and 6 the dispatching kernel is ~1 % faster (ptxas
-// arranges the two differently), so only FIX = 4 and 5 are built.
+// Measured on GB300: the kernel with loop 4 or 5 alone (the two-term rings of
+// a 512 x 512 image) is 4 % faster than the dispatching one, while for loops 1,
+// 2, 3 and 6 the dispatching kernel is ~1 % faster (ptxas arranges the two
+// differently), so only FIX = 4 and 5 are built.
 template <bool BF16, int FIX>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
