@@ -7,7 +7,8 @@
 // plus an r-pixel halo, at most 128 x 128 pixels) stays resident in tensor
 // memory as FP32 for all K terms.  For each term the region is streamed in
 // chunks of 16 rows:
-//   A  (compute warps) phase theta = 2 pi nu.f in FP32 radians, SFU cos/sin,
+//   A  (compute warps) phase t = nu.f in FP32 turns, reduced to [-1/2, 1/2] by
+//      t - rint(t), SFU cos/sin of 2 pi t,
 //      and the 8 modulated channels cos f_c, cos, sin f_c, sin of 16 rows x
 //      128 columns, stored as FP16/BF16 in the K-major operand layout
 //      (M = 16 rows x 8 channels = 128, K = columns);
@@ -523,11 +524,11 @@ __global__ void __launch_bounds__(kT, 1)
         // only through (row - r) & 7, a constant of the tile.
         const int rx = ring_xor((row - r) & 7), cb = 8 * xg + px0 - r;
         const int rcol0 = cb ^ rx, rcol1 = (cb + 1) ^ rx, rcol2 = (cb + 2) ^ rx, rcol3 = (cb + 3) ^ rx;
-        float nr0, nr1, nr2;  // frequency of the current term, radians per unit of f
+        float nr0, nr1, nr2;  // frequency of the current term, turns per unit of f
         auto load_nu = [&](int k) {
-            nr0 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k);
-            nr1 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k + 1);
-            nr2 = 6.28318530717958647692f * __ldg(nu_hi + 3 * k + 2);
+            nr0 = __ldg(nu_hi + 3 * k);
+            nr1 = __ldg(nu_hi + 3 * k + 1);
+            nr2 = __ldg(nu_hi + 3 * k + 2);
         };
         int pend_oc = -1, pend_slot = 0;
 
@@ -551,11 +552,12 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
                     const int j = 2 * p + u;
-                    // phase in radians; FP32 keeps its error near 1e-5 rad for |phase| <
-                    // 100, far below the 16-bit rounding of the channels
-                    const float tt = fmaf(nr0, f0[j], fmaf(nr1, f1[j], nr2 * f2[j]));
+                    // phase in turns, reduced to [-1/2, 1/2] before the SFU sin/cos
+                    // (Eq. Ht: theta = 2 pi nu.f), so the SFU argument stays within [-pi, pi]
+                    float tt = fmaf(nr0, f0[j], fmaf(nr1, f1[j], nr2 * f2[j]));
+                    tt -= rintf(tt);
                     float s_, c_;
-                    __sincosf(tt, &s_, &c_);
+                    __sincosf(6.28318530717958647692f * tt, &s_, &c_);
                     const bool v = (vm >> j) & 1u;
                     cv[u] = v ? c_ : 0.f;
                     sv[u] = v ? s_ : 0.f;
@@ -1023,12 +1025,10 @@ bool cost_before(const TcImg &a, const TcImg &b) {
     return a.r < b.r;
 }
 
-}  // namespace
-
-int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s) {
-    if (n <= 0) return BF_OK;
-    std::vector<unsigned char> host(tc_scratch_bytes(n), 0);  // control words (zero) + table
-    TcImg *tab = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
+// Fills, orders and finishes the table of a call; shared by both batch entry
+// points so that they launch identical work (a lone image gets its fitted
+// tile height in both).  m = number of non-empty images.
+int tc_prepare(const bf_item *items, int n, int variant, TcImg *tab, int *m_out, int *total, TcLayout *lay) {
     int m = 0;
     for (int i = 0; i < n; ++i) {
         if (items[i].H == 0 || items[i].W == 0) continue;
@@ -1036,12 +1036,32 @@ int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int
         if (rc != BF_OK) return rc;
         ++m;
     }
+    *m_out = m;
     if (m == 0) return BF_OK;
     if (m == 1) tc_fit_waves(tab[0]);
-    std::stable_sort(tab, tab + m, cost_before);
-    int total = 0;
+    for (int a = 1; a < m; ++a) {  // stable insertion sort by cost (no temporary buffer)
+        const TcImg t = tab[a];
+        int b = a - 1;
+        while (b >= 0 && cost_before(t, tab[b])) {
+            tab[b + 1] = tab[b];
+            --b;
+        }
+        tab[b + 1] = t;
+    }
+    tc_finish(tab, m, total, lay);
+    return BF_OK;
+}
+
+}  // namespace
+
+int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s) {
+    if (n <= 0) return BF_OK;
+    std::vector<unsigned char> host(tc_scratch_bytes(n), 0);  // control words (zero) + table
+    TcImg *tab = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
+    int m = 0, total = 0;
     TcLayout lay{};
-    tc_finish(tab, m, &total, &lay);
+    const int rc = tc_prepare(items, n, variant, tab, &m, &total, &lay);
+    if (rc != BF_OK || m == 0) return rc;
     const size_t bytes = (size_t)kCtrlWords * sizeof(int) + (size_t)m * sizeof(TcImg);
     if (cudaMemcpyAsync(scratch, host.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
         cudaGetLastError();
@@ -1112,37 +1132,29 @@ extern "C" int bf_filter_batch_noalloc(const bf_item *items, int n, int variant,
     if (n < 0 || (n > 0 && !items)) return BF_ERR_ARG;
     if (variant != BF_FP16TC && variant != BF_BF16TC) return BF_ERR_ARG;
     if (n > BF_NOALLOC_MAX_ITEMS) return BF_ERR_BUDGET;
+    cudaStream_t s = (cudaStream_t)stream;
+    // The uploads below copy from this call's stack; a captured graph would
+    // replay them after the frame is gone, so the call refuses capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return BF_ERR_ARG;
     for (int i = 0; i < n; ++i) {
         const int rc = check_image_args(items[i].plan, items[i].in, items[i].out, items[i].H, items[i].W,
                                         items[i].pitch);
         if (rc != BF_OK) return rc;
     }
     TcImg tab[BF_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap allocation either
-    int m = 0;
-    for (int i = 0; i < n; ++i) {
-        if (items[i].H == 0 || items[i].W == 0) continue;
-        const int rc = tc_fill(items[i], variant, tab[m]);
-        if (rc != BF_OK) return rc;
-        ++m;
-    }
-    if (m == 0) return BF_OK;
-    for (int a = 1; a < m; ++a) {  // stable insertion sort by cost (no temporary buffer)
-        const TcImg t = tab[a];
-        int b = a - 1;
-        while (b >= 0 && cost_before(t, tab[b])) {
-            tab[b + 1] = tab[b];
-            --b;
-        }
-        tab[b + 1] = t;
-    }
-    int total = 0;
+    int m = 0, total = 0;
     TcLayout lay{};
-    tc_finish(tab, m, &total, &lay);
+    const int rc = tc_prepare(items, n, variant, tab, &m, &total, &lay);
+    if (rc != BF_OK || m == 0) return rc;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BF_ERR_CUDA;
     char *scr = reinterpret_cast<char *>(noalloc_scratch(dev));
     if (!scr) return BF_ERR_CUDA;
-    cudaStream_t s = (cudaStream_t)stream;
     int *ctrl = reinterpret_cast<int *>(scr);
     TcImg *imgs = reinterpret_cast<TcImg *>(scr + kCtrlWords * sizeof(int));
     const int zero = 0;  // the tile counter must start at zero; the status word is left as is

@@ -5,8 +5,10 @@ loop).  Its scratch is a static device array instead of library-allocated
 memory.  Checked through the C ABI against bf_filter_batch, the entry point
 that allocates, on two calls in a row: the shared array keeps the previous
 call's contents, so the second call shows the counter is reset and the table
-rewritten.  This file is collected last and builds everything it needs, so it
-passes alone in a fresh process as well as after the other tests."""
+rewritten.  Both entry points build the same launch (one shared table
+preparation, including the tile height of a lone image), so the results must
+be bit-identical.  This file is collected last and builds everything it needs,
+so it passes alone in a fresh process as well as after the other tests."""
 import ctypes
 
 import numpy as np
@@ -18,8 +20,6 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
-TC_MAXABS = 0.5  # the tensor-core tolerance used by the parity tests
-
 
 @pytest.fixture(scope="module")
 def bf():
@@ -30,8 +30,8 @@ def bf():
     return _bf
 
 
-def _batch(bf):
-    specs = [(130, 200, 2.0, 32), (64, 64, 8.0, 64), (97, 150, 5.0, 32)]
+def _batch(bf, n=3):
+    specs = [(130, 200, 2.0, 32), (64, 64, 8.0, 64), (97, 150, 5.0, 32)][:n]
     plans, xs, items = [], [], []
     for i, (H, W, s, K) in enumerate(specs):
         f = synth.voronoi_image(H, W, 3, 7, 10.0, seed=900 + i)
@@ -49,12 +49,12 @@ def _items(bf, specs, plans, xs, outs):
     return arr
 
 
-@pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
-def test_noalloc_matches_allocating_entry_point_twice(bf, variant):
+@pytest.mark.parametrize("variant,n", [("fp16tc", 3), ("bf16tc", 3), ("fp16tc", 1)])
+def test_noalloc_matches_allocating_entry_point_twice(bf, variant, n):
     L = bf.lib()
     v = bf.VARIANTS[variant]
     stream = torch.cuda.current_stream().cuda_stream
-    specs, plans, xs = _batch(bf)
+    specs, plans, xs = _batch(bf, n)
     ref = [bf.pitched_empty(3, H, W) for (H, W, _, _) in specs]
     assert L.bf_filter_batch(_items(bf, specs, plans, xs, ref), len(specs), v, ctypes.c_void_p(stream)) == bf.BF_OK
     torch.cuda.synchronize()
@@ -68,7 +68,7 @@ def test_noalloc_matches_allocating_entry_point_twice(bf, variant):
         for y, r in zip(outs, ref):
             a, b = y.cpu().numpy(), r.cpu().numpy()
             assert np.isfinite(a).all()
-            assert np.abs(a - b).max() <= TC_MAXABS, f"call {call}"
+            assert np.array_equal(a, b), f"call {call}"
     assert bf.bf_last_status(stream) == bf.BF_OK
 
 
@@ -80,3 +80,20 @@ def test_noalloc_rejects_what_it_cannot_hold(bf):
     assert L.bf_filter_batch_noalloc(arr, bf.BF_NOALLOC_MAX_ITEMS + 1, bf.BF_FP16TC, None) == bf.BF_ERR_BUDGET
     assert L.bf_filter_batch_noalloc(arr, len(specs), bf.BF_FP32, None) == bf.BF_ERR_ARG
     assert L.bf_filter_batch_noalloc(arr, 0, bf.BF_FP16TC, None) == bf.BF_OK
+
+
+def test_noalloc_refuses_stream_capture(bf):
+    """The call uploads its table from host memory of the call itself, which a
+    captured graph would read again at every replay; under capture it returns
+    BF_ERR_ARG and queues nothing."""
+    L = bf.lib()
+    specs, plans, xs = _batch(bf, 1)
+    outs = [bf.pitched_empty(3, H, W) for (H, W, _, _) in specs]
+    arr = _items(bf, specs, plans, xs, outs)
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    rc = None
+    with torch.cuda.graph(g, stream=s):
+        rc = L.bf_filter_batch_noalloc(arr, 1, bf.BF_FP16TC, ctypes.c_void_p(s.cuda_stream))
+    assert rc == bf.BF_ERR_ARG
