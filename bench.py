@@ -47,11 +47,12 @@ def algorithmic_flops_per_pixel(d: int, r: int, K: int) -> float:
 MEASURED_TRAFFIC = {
     "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "72bbe6ac7b91740937590dcfe38310efcff2c38d",
                "workload": "4k", "bytes_per_launch": 100.601e6 + 58.787e6,
-               "capture": "ncu --set full of one launch on this workload (profiles/mcsf_tc_4k_s8_K128.md)"},
+               "capture": "ncu --set full --clock-control none -k regex:mcsf_tc -s 2 -c 1, one launch of "
+                          "bench.py --steps 2 --warmup 3 --variant fp16tc --no-cpu-baseline --no-fp32-compare"},
     "fp32rec": {"src": "paper_1605_02164_gb300/csrc/bf_recursive.cu", "sha1": "ae50e6fedcb753639417caa1d0166d124187c5a9",
                 "bytes_per_pixel_term": (1.966 + 3.941 + 7.515 + 3.207) * 1e9 / (64 * 1024 * 1024),
-                "capture": "ncu --set full of one row and one column launch (64 terms) on 1024x1024 "
-                           "(profiles/mcsf_recursive_1024_s5_K64.md), scaled by pixels x terms"},
+                "capture": "ncu --set full --clock-control none of one row and one column launch (64 terms) of "
+                           "bench.py --workload mid --variant fp32rec, scaled by pixels x terms"},
 }
 
 
@@ -321,9 +322,10 @@ def run_ours(args):
                 "bytes_kind": "design traffic of the two-pass recursion (FP32 X, V, P/Z planes in HBM)"}
     elif variant == bf.BF_FP32:
         sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
         roof = {"bound": "alu", "achieved": flops / (kernel_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "peak_source": f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})"}
+                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz, {peak_src})"}
     else:
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor", "achieved": flops / (kernel_ms / 1e3) / 1e12, "peak": peak, "unit": "TFLOP/s",
@@ -333,6 +335,8 @@ def run_ours(args):
         roof["traffic"], roof["traffic_source"] = args.traffic, "--traffic"
     else:
         roof["traffic"], roof["traffic_source"] = measured_traffic(args.variant, args.workload, pixels, w.K)
+    if roof["traffic"] is not None:
+        roof["traffic_kind"] = "from a stored ncu capture of this kernel source (dram__bytes_read + write), not measured in this run"
     if roof["bound"] != "hbm":
         roof["flops_per_launch"] = flops
 
@@ -381,6 +385,19 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
+    if ws == 1 and not args.no_extras:
+        # the batched and served forms on the same GPU, after the timed region:
+        # one persistent launch over the uneven 64-image batch, and the Poisson
+        # serving trace through the request loop, each against plain FP32 launches
+        bl = batch_line(args)
+        line["batched"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "images_per_s",
+                                             "per_image_launches_mpx", "plain_fp32_mpx")}
+        line["batched"]["workload"] = bl["config"]["workload"]
+        sl = serve_line(args)
+        sv, pl = sl["served"], sl["plain_fp32_per_image"]
+        line["served"] = {"images_per_s": sv["images_per_s"], "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
+                          "plain_fp32_images_per_s": pl["images_per_s"], "plain_fp32_p99_ms": pl["p99_ms"],
+                          "requests": sl["config"]["requests"], "workload": sl["config"]["workload"]}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -394,7 +411,7 @@ def _split_items(bf, items_and_d, variant):
     return tc, fp
 
 
-def run_batch(args):
+def batch_line(args):
     """Uneven batch: 64 images, sizes U[256, 2048] x U[256, 1536], d in {3, 6},
     sigma_s ~ U[2, 10], C with condition number <= 10, K in {32, 64, 128}.
     One persistent launch (d = 3 on the tensor cores, d = 6 on the FP32
@@ -450,11 +467,15 @@ def run_batch(args):
                        "images": len(ws), "mpixel": px / 1e6, "d3_images": len(tc), "d6_images": len(fp)},
             "per_image_launches_mpx": px / ms_single / 1e3, "plain_fp32_mpx": px / ms_fp32 / 1e3,
             "images_per_s": len(ws) / ms_batch * 1e3}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_batch(args):
+    print(json.dumps(batch_line(args)), flush=True)
     return 0
 
 
-def run_serve(args):
+def serve_line(args):
     """Open-loop Poisson trace (2000 requests/s) of square RGB images with area
     log-uniform in [512^2, 4096^2], sigma_s ~ U[2, 10], C = sigma_r^2 I with
     sigma_r ~ U[20, 60], K = 64, through the request loop (continuous batching
@@ -546,7 +567,11 @@ def run_serve(args):
                        "streams": 3, "max_batch": 64},
             "served": served, "plain_fp32_per_image": plain,
             "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"]}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+def run_serve(args):
+    print(json.dumps(serve_line(args)), flush=True)
     return 0
 
 
@@ -677,6 +702,8 @@ def main():
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served measurements that follow the headline")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

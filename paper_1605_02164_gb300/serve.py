@@ -59,6 +59,7 @@ class Request:
     t_done: float = math.nan
     status: int = 1  # 1 pending, 0 done, < 0 BF_ERR_* or CANCELLED
     _bytes: int = 0
+    _ready: object = None  # CUDA event on the submitting stream: x is complete once it fires
     done_evt: threading.Event = field(default_factory=threading.Event)
 
     @property
@@ -113,8 +114,15 @@ class Server:
 
     # -- client side -------------------------------------------------------------------
     def submit(self, req: Request) -> Request:
+        """Queue a request.  Its input may still be in production on the caller's
+        current stream: the batch that filters it waits for the work queued there
+        up to this call, and the input's memory stays reserved until that batch
+        has read it, even if the caller drops its reference."""
         if not req.t_arrival:
             req.t_arrival = time.perf_counter()
+        torch = self.torch
+        req._ready = torch.cuda.Event()
+        req._ready.record(torch.cuda.current_stream(req.x.device))
         d, H, W = req.x.shape
         req._bytes = d * H * req.x.stride(1) * 4
         r = int(math.floor(3.0 * req.sigma_s + 1e-9))
@@ -203,6 +211,9 @@ class Server:
         with torch.cuda.stream(s):
             for r in batch:
                 r.t_admit = now
+                if r._ready is not None:
+                    s.wait_event(r._ready)  # the input's producer work on the submitting stream
+                r.x.record_stream(s)        # keep x's memory until this stream has read it
                 d, H, W = r.x.shape
                 r.out = torch.empty_strided(r.x.shape, r.x.stride(), dtype=torch.float32, device=self.dev)
                 p = self.plan(d, r.C, r.sigma_s, r.N, r.K, r.seed, r.whiten)

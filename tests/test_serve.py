@@ -145,3 +145,32 @@ def test_cancelled_request_is_not_run(bf):
     assert srv.used == 0 and srv.cancelled == [victim]
     for r in rest:
         assert np.array_equal(r.out.cpu().numpy(), _alone(bf, r, bf.BF_FP16TC)), r.rid
+
+
+def test_input_produced_on_the_submitting_stream(bf):
+    """A request whose input is still being written on the caller's stream when
+    it is submitted (no synchronisation in between): the batch waits for that
+    work, so the result equals filtering the finished input alone."""
+    from paper_1605_02164_gb300.serve import Server
+    v = bf.BF_FP16TC
+    ref = _requests(bf, 6, seed=11)
+    srcs = [r.x.clone() for r in ref]
+    torch.cuda.synchronize()
+    producer = torch.cuda.Stream()
+    srv = Server(budget_bytes=64 << 20, streams=2, max_batch=3, variant=v).start()
+    busy = torch.empty(4096, 4096, device="cuda")
+    reqs = []
+    with torch.cuda.stream(producer):
+        for r, src in zip(ref, srcs):
+            x = bf.pitched_empty(*src.shape)
+            x.fill_(float("nan"))
+            busy.normal_()
+            busy = busy @ busy  # keeps the producer stream busy before the copy lands
+            x.copy_(src)
+            reqs.append(srv.submit(type(r)(x, r.C, r.sigma_s, r.K, r.N, seed=r.seed, rid=r.rid)))
+    for r in reqs:
+        assert r.done_evt.wait(120)
+    srv.close()
+    assert all(r.status == 0 for r in reqs)
+    for r, r0 in zip(reqs, ref):
+        assert np.array_equal(r.out.cpu().numpy(), _alone(bf, r0, v)), r.rid
