@@ -235,6 +235,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
     pitch = x.stride(1)
+    tuning = {"mode": "not tunable (whole-image recursion)"}
+    if variant != bf.BF_FP32_RECURSIVE:
+        groups = [([(variant, w.d, plan.r, w.H, w.W, bf.BF_TUNE_ALONE)], w.K)]
+        if variant != bf.BF_FP32 and not args.no_fp32_compare:
+            groups.append(([(bf.BF_FP32, w.d, plan.r, w.H, w.W, bf.BF_TUNE_ALONE)], min(w.K, 32)))
+        tuning = setup_tuning(args, groups)
 
     def step():
         bf.bf_filter(plan, x.data_ptr(), y.data_ptr(), w.H, w.W, pitch, variant, sp)
@@ -372,6 +378,7 @@ def run_ours(args):
                    "plan": "built once outside the timed region", "parallelism": f"replicas x{ws}"},
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99))},
         "plan_ms": plan_ms,
+        "tuning": tuning,
         "fp32_value": fp32_mpx,
         "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": int(f.nbytes),
                 "d2h_bytes_per_step": int(f.nbytes), "api": "bf_filter_host_async, steps alternating over two streams (pinned host buffers)",
@@ -391,17 +398,46 @@ def run_ours(args):
         # serving trace through the request loop, each against plain FP32 launches
         bl = batch_line(args)
         line["batched"] = {k: bl[k] for k in ("value", "unit", "ms_per_step", "images_per_s",
-                                             "per_image_launches_mpx", "plain_fp32_mpx")}
+                                             "per_image_launches_mpx", "plain_fp32_mpx", "untuned_mpx")}
+        line["batched"]["tuning"] = {k: v for k, v in bl["tuning"].items() if k != "tile_rows"}
         line["batched"]["workload"] = bl["config"]["workload"]
         sl = serve_line(args)
         sv, pl = sl["served"], sl["plain_fp32_per_image"]
         line["served"] = {"images_per_s": sv["images_per_s"], "p50_ms": sv["p50_ms"], "p99_ms": sv["p99_ms"],
                           "plain_fp32_images_per_s": pl["images_per_s"], "plain_fp32_p99_ms": pl["p99_ms"],
-                          "requests": sl["config"]["requests"], "workload": sl["config"]["workload"]}
+                          "requests": sl["config"]["requests"], "workload": sl["config"]["workload"],
+                          "tuning": {k: v for k, v in sl["tuning"].items() if k != "tile_rows"}}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def setup_tuning(args, groups):
+    """Tile heights for the (variant, d, r, H, W, context) keys of each
+    (keys, K) group, timed at K terms: loaded from the
+    tuning cache, and timed now (tune.py, CUDA events) for the keys it lacks;
+    outside every timed region.  --tune off leaves the table empty (the
+    kernels' cost models).  Returns what the JSON line reports."""
+    from paper_1605_02164_gb300 import bf, tune
+    bf.bf_tune_clear()
+    if args.tune == "off":
+        return {"mode": "off (cost models)"}
+    cache = tune.TuneCache(args.tune_cache)
+    timed, secs, chosen = 0, 0.0, {}
+    for keys, K in groups:
+        s = cache.ensure(keys, K=K)
+        timed, secs = timed + s["tuned"], secs + s["seconds"]
+        for v, d, r, H, W, ctx in keys:
+            k = cache.key(v, d, r, bf.bf_tune_size_class(H, W), ctx)
+            chosen[k] = cache.entries[k]["rows"]
+    try:
+        cache.save()
+    except OSError:
+        pass
+    return {"mode": "measured (tune.py)", "cache": cache.path, "keys_timed_now": timed,
+            "entries": len(cache.entries), "tuning_seconds": round(secs, 2),
+            "key": "variant:d:ceil(r/8):size class:context (0 alone, 1 batch)", "tile_rows": chosen}
 
 
 def _split_items(bf, items_and_d, variant):
@@ -457,6 +493,13 @@ def batch_line(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    keys = []
+    for (it, d), w in zip(items, ws):
+        v = variant if (d == 3 and variant != bf.BF_FP32) else bf.BF_FP32
+        keys.append((v, d, it[0].r, w.H, w.W, bf.BF_TUNE_BATCH))
+    bf.bf_tune_clear()
+    ms_untuned = timed(batched, args.steps)       # the kernels' cost models (tallest tiles)
+    tuning = setup_tuning(args, [(keys, 4)])
     ms_batch = timed(batched, args.steps)
     ms_single = timed(lambda: per_image(variant), max(1, args.steps // 2))
     ms_fp32 = timed(lambda: per_image(bf.BF_FP32), 1)
@@ -466,7 +509,8 @@ def batch_line(args):
             "config": {"workload": f"batch{len(ws)}_sizes256-2048x256-1536_d3or6_s2-10_K32-128",
                        "images": len(ws), "mpixel": px / 1e6, "d3_images": len(tc), "d6_images": len(fp)},
             "per_image_launches_mpx": px / ms_single / 1e3, "plain_fp32_mpx": px / ms_fp32 / 1e3,
-            "images_per_s": len(ws) / ms_batch * 1e3}
+            "images_per_s": len(ws) / ms_batch * 1e3, "untuned_mpx": px / ms_untuned / 1e3,
+            "untuned_ms": ms_untuned, "tuning": tuning}
     return line
 
 
@@ -513,7 +557,20 @@ def serve_line(args):
         return t0, reqs
 
     variant = bf.VARIANTS[args.variant]
-    srv = Server(budget_bytes=40 << 30, streams=3, max_batch=64, variant=variant).start()
+    keys = {}
+    for _, w in trace:
+        v = variant if variant != bf.BF_FP32_RECURSIVE else None
+        if v is None:
+            break
+        r = int(math.floor(3.0 * w.sigma_s + 1e-9))
+        for ctx in (bf.BF_TUNE_ALONE, bf.BF_TUNE_BATCH):
+            keys.setdefault((v, (r + 7) // 8, bf.bf_tune_size_class(w.H, w.W), ctx),
+                            (v, 3, r, w.H, w.W, ctx))
+    tuning = setup_tuning(args, [(list(keys.values()), 8)]) if keys else {"mode": "not tunable"}
+    if "tile_rows" in tuning:
+        tuning["tile_rows"] = len(tuning["tile_rows"])
+    srv = Server(budget_bytes=40 << 30, streams=3, max_batch=64, variant=variant,
+                 tune_cache=tuning.get("cache")).start()
     t0, reqs = replay(srv.submit)
     for r in reqs:
         r.done_evt.wait()
@@ -565,7 +622,7 @@ def serve_line(args):
             "config": {"workload": "serve_poisson2000_rgb512-4096_s2-10_sr20-60_K64",
                        "arrival_seconds": args.serve_seconds, "requests": len(trace), "budget_gb": 40,
                        "streams": 3, "max_batch": 64},
-            "served": served, "plain_fp32_per_image": plain,
+            "served": served, "plain_fp32_per_image": plain, "tuning": tuning,
             "latency_ms": {"p50": served["p50_ms"], "p99": served["p99_ms"]}}
     return line
 
@@ -606,24 +663,41 @@ def run_sigma_sweep(args):
             ts.append(a.elapsed_time(b))
         return float(np.median(ts))
 
+    # each windowed path is timed with the kernels' cost models and then with
+    # the tile heights measured for its key (tune.py, at K = 32)
+    tunable = [n for n in dict.fromkeys((args.variant, "fp32")) if n != "fp32rec"]
+    sigmas = (1.0, 2.0, 3.0, 4.0, 5.0, 10.0)
+    keys = [(bf.VARIANTS[n], 3, int(math.floor(3.0 * s + 1e-9)), H, W, bf.BF_TUNE_ALONE)
+            for H, W in ((512, 512), (2160, 3840)) for s in sigmas for n in tunable]
     rows = []
     for H, W in ((512, 512), (2160, 3840)):
         f = synth.voronoi_image(H, W, 3, 16, 10.0, seed=args.seed + H)
         x = bf.to_pitched(f)
         y = bf.pitched_empty(3, H, W)
-        for s in (1.0, 2.0, 3.0, 4.0, 5.0, 10.0):
+        for s in sigmas:
             p = bf.bf_plan(3, C, s, 10, 300, args.seed + int(10 * s))
             row = {"H": H, "W": W, "sigma_s": s, "r": p.r}
-            for name in (args.variant, "fp32", "fp32rec"):
-                ms = median_ms(p, x, y, bf.VARIANTS[name])
-                row[f"{name}_ms"] = ms
-                row[f"{name}_mpx"] = H * W / ms / 1e3
-            rows.append(row)
+            bf.bf_tune_clear()
+            for name in tunable:
+                row[f"{name}_untuned_ms"] = median_ms(p, x, y, bf.VARIANTS[name])
+            rows.append((row, p, x, y))
+    tuning = setup_tuning(args, [(keys, 32)])
+    for row, p, x, y in rows:
+        H, W = row["H"], row["W"]
+        for name in (args.variant, "fp32", "fp32rec"):
+            ms = median_ms(p, x, y, bf.VARIANTS[name])
+            row[f"{name}_ms"] = ms
+            row[f"{name}_mpx"] = H * W / ms / 1e3
+            if name in tunable:
+                row[f"{name}_rows"] = bf.bf_tune_get(bf.VARIANTS[name], 3, p.r, bf.bf_tune_size_class(H, W),
+                                                     bf.BF_TUNE_ALONE)
+    rows = [row for row, *_ in rows]
     if bf.bf_last_status(sp) != bf.BF_OK:
         raise RuntimeError("device status after the sweep")
     line = {"metric": "ms per image vs sigma_s (RGB, sigma_r=40, N=10, T=300)", "unit": "ms",
             "higher_is_better": False, "n_gpus": 1, "steps": reps, "dtype": args.variant, "data": "synthetic",
-            "config": {"workload": "sigma_sweep_rgb_512x512_and_3840x2160_sr40_N10_T300"}, "rows": rows}
+            "config": {"workload": "sigma_sweep_rgb_512x512_and_3840x2160_sr40_N10_T300"}, "rows": rows,
+            "tuning": {k: v for k, v in tuning.items() if k != "tile_rows"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -702,6 +776,9 @@ def main():
                     help="DRAM bytes per launch of the fused kernel from an ncu capture")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32-compare", action="store_true")
+    ap.add_argument("--tune", default="auto", choices=["auto", "off"],
+                    help="tile heights: measured per key and cached (auto), or the kernels' cost models (off)")
+    ap.add_argument("--tune-cache", default=None, help="tuning cache file (default: $BF_TUNE_CACHE or ~/.cache/libbf)")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the batched and served measurements that follow the headline")
     args = ap.parse_args()

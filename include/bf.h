@@ -180,8 +180,9 @@ int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
  *                   before any work is queued (split the batch).
  * Results are identical to bf_filter_batch with the same arguments.
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress (with that device current) and caches it; make that
- * first call before any stream capture.  All calls share the one array and
+ * cudaGetSymbolAddress (with that device current) and caches it.  The call
+ * uploads its table from host memory of the call itself, so it returns
+ * BF_ERR_ARG on a stream that is being captured.  All calls share the one array and
  * it keeps the last call's contents: each call resets the tile counter and
  * rewrites the table, so calls whose work overlaps on the GPU (on different
  * streams, or from several host threads) race and must be serialised by the
@@ -189,6 +190,38 @@ int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
  */
 #define BF_NOALLOC_MAX_ITEMS 256
 int bf_filter_batch_noalloc(const bf_item *items, int n, int variant, void *stream);
+
+/*
+ * Tuning of the windowed kernels' tile height.  The paper has no counterpart:
+ * it is a service of the library (the batched and served forms pick their
+ * tiles from measurements; the paper's own Table 1 axis is sigma_s, i.e. r).
+ *
+ * The tile height (output rows per CTA tile, a multiple of 16) of the
+ * BF_FP32, BF_FP16TC and BF_BF16TC kernels changes no result, only how the
+ * work spreads over the SMs and how much of the r-pixel halo each tile
+ * recomputes.  Without an entry a launch uses its cost model (tile waves x
+ * steps per tile for an image alone, the tallest tile in a batch).  Entries
+ * are keyed by (variant, d, radius class, size class, context):
+ *   radius class ceil(r / 8): r = 0, 1..8, 9..16, 17..24, 25..32 (the classes
+ *                share the tensor-core tile geometry); set or get with any r
+ *                of the class
+ *   size class   bf_tune_size_class(H, W) = 32 floor(2 log2 H) + floor(2 log2 W)
+ *                (half-octave classes of height and width)
+ *   context      BF_TUNE_ALONE: the image is the only one of its launch
+ *                (bf_filter, a batch of one); BF_TUNE_BATCH: one of several
+ *                images of one persistent launch (or of the forked FP32 batch)
+ *   tile_rows    16..128 in steps of 16; a launch clamps it to what its
+ *                window and shared memory allow; 0 removes the entry
+ * The table is process-wide and thread-safe; tune.py fills it from timings
+ * and keeps a JSON cache.  Returns BF_OK or BF_ERR_ARG (bad key or value).
+ */
+#define BF_TUNE_ALONE 0
+#define BF_TUNE_BATCH 1
+int bf_tune_size_class(int H, int W); /* the class, or BF_ERR_ARG for H or W <= 0 */
+int bf_tune_set(int variant, int d, int r, int size_class, int context, int tile_rows);
+int bf_tune_get(int variant, int d, int r, int size_class, int context, int *tile_rows); /* 0: none */
+int bf_tune_clear(void);
+int bf_tune_count(void); /* number of entries */
 
 /*
  * bf_filter_host -- end-to-end convenience call for callers holding host

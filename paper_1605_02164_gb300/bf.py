@@ -98,6 +98,9 @@ def _load():
         lib.bf_error_string.argtypes = [i]
         lib.bf_error_string.restype = ctypes.c_char_p
         lib.bf_version.restype = i
+        lib.bf_tune_size_class.argtypes = [i, i]
+        lib.bf_tune_set.argtypes = [i, i, i, i, i, i]
+        lib.bf_tune_get.argtypes = [i, i, i, i, i, ctypes.POINTER(i)]
         _lib = lib
         return lib
 
@@ -242,6 +245,35 @@ def bf_last_status(stream: int = 0) -> int:
 
 def bf_version() -> int:
     return int(_load().bf_version())
+
+
+BF_TUNE_ALONE = 0
+BF_TUNE_BATCH = 1
+
+
+def bf_tune_size_class(H: int, W: int) -> int:
+    c = int(_load().bf_tune_size_class(int(H), int(W)))
+    if c < 0:
+        raise BFError(c, "bf_tune_size_class")
+    return c
+
+
+def bf_tune_set(variant: int, d: int, r: int, size_class: int, context: int, tile_rows: int) -> None:
+    _check(_load().bf_tune_set(variant, d, r, size_class, context, tile_rows), "bf_tune_set")
+
+
+def bf_tune_get(variant: int, d: int, r: int, size_class: int, context: int) -> int:
+    out = ctypes.c_int(0)
+    _check(_load().bf_tune_get(variant, d, r, size_class, context, ctypes.byref(out)), "bf_tune_get")
+    return int(out.value)
+
+
+def bf_tune_clear() -> None:
+    _check(_load().bf_tune_clear(), "bf_tune_clear")
+
+
+def bf_tune_count() -> int:
+    return int(_load().bf_tune_count())
 
 
 def bf_debug_inject(faults: int) -> None:

@@ -321,7 +321,11 @@ int fit_waves(int r, int H, int W, int BY) {
 template <int D, int G>
 int launch_dg(const bf_plan_s &p, const float *in, float *out, int H, int W, int pitch, int BY, cudaStream_t s,
               bool alone) {
-    if (alone) BY = fit_waves(p.r, H, W, BY);
+    const int tuned = tune_rows(BF_FP32, D, p.r, H, W, alone ? BF_TUNE_ALONE : BF_TUNE_BATCH);
+    if (tuned > 0)
+        BY = tuned < BY ? tuned : BY;  // a measured height, within what fits
+    else if (alone)
+        BY = fit_waves(p.r, H, W, BY);
     const Geom g = make_geom<D, G>(p.r, BY);
     const size_t bytes = g.smem_floats * sizeof(float);
     cudaError_t e = cudaFuncSetAttribute(mcsf_fp32_kernel<D, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

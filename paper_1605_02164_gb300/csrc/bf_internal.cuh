@@ -60,6 +60,10 @@ int launch_tc(const bf_plan_s &p, const float *in, float *out, int H, int W, int
 size_t tc_scratch_bytes(int n);
 int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s);
 
+// Tuned tile height (output rows) for an image of H x W in `context`
+// (BF_TUNE_ALONE / BF_TUNE_BATCH), or 0 when the table has no entry (bf_tune.cu).
+int tune_rows(int variant, int d, int r, int H, int W, int context);
+
 // Library-owned device scratch for work issued on `stream`, at least `bytes`
 // long (grown on demand; calls on one stream are ordered, so they may share it).
 void *stream_scratch(cudaStream_t stream, size_t bytes);

@@ -915,6 +915,14 @@ int tc_fill(const bf_item &it, int variant, TcImg &g) {
 // per tile), so that a small image spreads over all SMs.  A pixel's arithmetic
 // does not depend on it: tile origins stay multiples of 16 rows.  Batches keep
 // the tallest tile; their queue balances the SMs.
+// Output rows of a tile: 16 noc, at most what the geometry allows (noc_max).
+void tc_set_noc(TcImg &g, int noc, int noc_max) {
+    if (noc > noc_max) noc = noc_max;
+    if (noc < 1) noc = 1;
+    g.BY = 16 * noc;
+    g.nc = cdiv(g.BY + 2 * g.r, 16);
+}
+
 void tc_fit_waves(TcImg &g) {
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -1038,7 +1046,16 @@ int tc_prepare(const bf_item *items, int n, int variant, TcImg *tab, int *m_out,
     }
     *m_out = m;
     if (m == 0) return BF_OK;
-    if (m == 1) tc_fit_waves(tab[0]);
+    // tile height: a measured one from the tuning table, else the cost model
+    // (tc_fit_waves alone; the geometry's tallest tile in a batch)
+    const int ctx = m == 1 ? BF_TUNE_ALONE : BF_TUNE_BATCH;
+    for (int i = 0; i < m; ++i) {
+        const int rows = tune_rows(variant, 3, tab[i].r, tab[i].H, tab[i].W, ctx);
+        if (rows > 0)
+            tc_set_noc(tab[i], rows / 16, tab[i].BY / 16);
+        else if (m == 1)
+            tc_fit_waves(tab[i]);
+    }
     for (int a = 1; a < m; ++a) {  // stable insertion sort by cost (no temporary buffer)
         const TcImg t = tab[a];
         int b = a - 1;

@@ -69,9 +69,17 @@ class Request:
 
 class Server:
     def __init__(self, budget_bytes: int = 40 << 30, streams: int = 2, max_batch: int = 64,
-                 variant: int = bf.BF_FP16TC, plan_cache: int = 1024, device: int = 0):
+                 variant: int = bf.BF_FP16TC, plan_cache: int = 1024, device: int = 0, tune_cache=None):
+        """tune_cache: a tune.TuneCache or the path of its JSON file; its tile
+        heights go into the library's table before the loop starts, so every
+        batch the loop launches takes the measured heights."""
         import torch
         self.torch = torch
+        self.tuned_entries = 0
+        if tune_cache is not None:
+            from .tune import TuneCache
+            cache = tune_cache if isinstance(tune_cache, TuneCache) else TuneCache(str(tune_cache))
+            self.tuned_entries = cache.apply()
         self.dev = torch.device("cuda", device)
         self.budget = int(budget_bytes)
         self.used = 0

@@ -111,3 +111,78 @@ def test_fault_injection_host_side(lib):
         assert not h.value
     finally:
         assert L.bf_debug_inject(0) == bf.BF_OK
+
+
+def test_tuning_table(lib):
+    """bf_tune_*: keys by radius class ceil(r / 8), values 16..128 in steps of
+    16, 0 removes; bad keys are refused.  Host-only (no CUDA call)."""
+    from paper_1605_02164_gb300 import bf
+    bf.bf_tune_clear()
+    try:
+        cls = bf.bf_tune_size_class(2160, 3840)
+        assert cls == 32 * 22 + 23                       # floor(2 log2 2160) = 22, floor(2 log2 3840) = 23
+        assert bf.bf_tune_size_class(512, 512) == 32 * 18 + 18
+        assert bf.bf_tune_size_class(1, 1) == 0
+        assert bf.lib().bf_tune_size_class(0, 5) == bf.BF_ERR_ARG
+        bf.bf_tune_set(bf.BF_FP16TC, 3, 24, cls, bf.BF_TUNE_ALONE, 48)
+        assert bf.bf_tune_get(bf.BF_FP16TC, 3, 24, cls, bf.BF_TUNE_ALONE) == 48
+        assert bf.bf_tune_get(bf.BF_FP16TC, 3, 17, cls, bf.BF_TUNE_ALONE) == 48   # same radius class
+        assert bf.bf_tune_get(bf.BF_FP16TC, 3, 25, cls, bf.BF_TUNE_ALONE) == 0    # next class
+        assert bf.bf_tune_get(bf.BF_FP16TC, 3, 24, cls, bf.BF_TUNE_BATCH) == 0
+        assert bf.bf_tune_get(bf.BF_BF16TC, 3, 24, cls, bf.BF_TUNE_ALONE) == 0
+        assert bf.bf_tune_count() == 1
+        bf.bf_tune_set(bf.BF_FP32, 6, 3, cls, bf.BF_TUNE_BATCH, 128)
+        assert bf.bf_tune_count() == 2
+        bf.bf_tune_set(bf.BF_FP16TC, 3, 20, cls, bf.BF_TUNE_ALONE, 0)             # removes the class entry
+        assert bf.bf_tune_count() == 1
+        L = bf.lib()
+        out = ctypes.c_int()
+        for bad in [(bf.BF_FP32_RECURSIVE, 3, 4, cls, 0, 32), (7, 3, 4, cls, 0, 32), (0, 0, 4, cls, 0, 32),
+                    (0, 9, 4, cls, 0, 32), (0, 3, 33, cls, 0, 32), (0, 3, -1, cls, 0, 32), (0, 3, 4, -1, 0, 32),
+                    (0, 3, 4, cls, 2, 32), (0, 3, 4, cls, 0, 24), (0, 3, 4, cls, 0, 144), (0, 3, 4, cls, 0, -16)]:
+            assert L.bf_tune_set(*bad) == bf.BF_ERR_ARG, bad
+        assert L.bf_tune_get(0, 3, 4, cls, 0, None) == bf.BF_ERR_ARG
+        assert L.bf_tune_get(0, 3, 4, cls, 3, ctypes.byref(out)) == bf.BF_ERR_ARG
+        assert bf.bf_tune_count() == 1
+    finally:
+        bf.bf_tune_clear()
+    assert bf.bf_tune_count() == 0
+
+
+def test_tune_cache_round_trip(lib, tmp_path):
+    """A saved cache applied in a clean table restores the same entries."""
+    from paper_1605_02164_gb300 import bf, tune
+    path = str(tmp_path / "tune.json")
+    c = tune.TuneCache(path)
+    assert c.entries == {}
+    cls = bf.bf_tune_size_class(1024, 1024)
+    for v, d, r, ctx, rows in [(bf.BF_FP16TC, 3, 9, bf.BF_TUNE_ALONE, 64), (bf.BF_FP32, 6, 30, bf.BF_TUNE_BATCH, 96)]:
+        c.entries[c.key(v, d, r, cls, ctx)] = {"variant": v, "d": d, "r": r, "size_class": cls, "context": ctx,
+                                               "rows": rows}
+    c.save()
+    bf.bf_tune_clear()
+    try:
+        c2 = tune.TuneCache(path)
+        assert c2.apply() == 2 and bf.bf_tune_count() == 2
+        assert bf.bf_tune_get(bf.BF_FP16TC, 3, 16, cls, bf.BF_TUNE_ALONE) == 64
+        assert bf.bf_tune_get(bf.BF_FP32, 6, 25, cls, bf.BF_TUNE_BATCH) == 96
+        assert c2.has(bf.BF_FP16TC, 3, 12, 1100, 1050, bf.BF_TUNE_ALONE)   # same half-octave classes
+        assert not c2.has(bf.BF_FP16TC, 3, 12, 1100, 1000, bf.BF_TUNE_ALONE)
+        assert not c2.has(bf.BF_FP16TC, 3, 17, 1024, 1024, bf.BF_TUNE_ALONE)
+        assert tune.candidates(bf.BF_FP16TC, 24, 2160) == [16, 32, 48, 64, 80]
+        assert tune.candidates(bf.BF_FP16TC, 32, 2160) == [16, 32, 48, 64]
+        assert tune.candidates(bf.BF_FP32, 3, 40) == [16, 32, 48]
+    finally:
+        bf.bf_tune_clear()
+
+
+def test_tune_cache_drops_entries_of_other_sources(tmp_path):
+    import json
+    from paper_1605_02164_gb300 import tune
+    path = str(tmp_path / "old.json")
+    with open(path, "w") as fh:
+        json.dump({"identity": {"library": "0" * 16, "device": None},
+                   "entries": {"1:3:3:600:0": {"variant": 1, "d": 3, "r": 24, "size_class": 600, "context": 0,
+                                               "rows": 48}}}, fh)
+    c = tune.TuneCache(path)
+    assert c.entries == {} and c.dropped == 1

@@ -174,3 +174,37 @@ def test_input_produced_on_the_submitting_stream(bf):
     assert all(r.status == 0 for r in reqs)
     for r, r0 in zip(reqs, ref):
         assert np.array_equal(r.out.cpu().numpy(), _alone(bf, r0, v)), r.rid
+
+
+def test_loop_with_tuning_cache_gives_untuned_results(bf, tmp_path):
+    """A server started with a tuning cache applies it (every class of the
+    trace gets 16-row tiles, far from the cost model's choice) and still
+    returns each request's untuned, alone result bit for bit."""
+    from paper_1605_02164_gb300.serve import Server
+    from paper_1605_02164_gb300.tune import TuneCache
+    v = bf.BF_FP16TC
+    reqs = _requests(bf, 10, seed=11)
+    bf.bf_tune_clear()
+    expect = [_alone(bf, r, v) for r in reqs]
+    cache = TuneCache(str(tmp_path / "tune.json"))
+    for r in reqs:
+        d, H, W = r.x.shape
+        rad = int(np.floor(3.0 * r.sigma_s + 1e-9))
+        cls = bf.bf_tune_size_class(H, W)
+        for var in (bf.BF_FP16TC, bf.BF_FP32):
+            for ctx in (bf.BF_TUNE_ALONE, bf.BF_TUNE_BATCH):
+                cache.entries[cache.key(var, d, rad, cls, ctx)] = {"variant": var, "d": d, "r": rad,
+                                                                  "size_class": cls, "context": ctx, "rows": 16}
+    cache.save()
+    try:
+        srv = Server(budget_bytes=64 << 20, streams=2, max_batch=4, variant=v, tune_cache=cache.path).start()
+        assert srv.tuned_entries == len(cache.entries) == bf.bf_tune_count()
+        for r in reqs:
+            srv.submit(r)
+        for r in reqs:
+            assert r.done_evt.wait(120)
+        srv.close()
+        for r, e in zip(reqs, expect):
+            assert r.status == 0 and np.array_equal(r.out.cpu().numpy(), e), r.rid
+    finally:
+        bf.bf_tune_clear()
