@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(kT, 1)
 
     // ---- compute warps --------------------------------------------------------------------
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegsCompute));
-    int band_r = -1;            // window radius the Toeplitz bands in smem were built for
+    const uint16_t *band_taps = nullptr;  // the taps the Toeplitz bands in smem were built from
     uint32_t ph1 = 0, ph2 = 0;  // phases of mbar[0], mbar[1] (carry over from tile to tile)
     for (;;) {
         bool timed_out = false;  // a wait on the tensor core ran out
@@ -464,7 +464,11 @@ __global__ void __launch_bounds__(kT, 1)
         const int rx0 = tx0 - r, ry0 = ty0 - r;
         const size_t plane = (size_t)H * pitch;
 
-        if (r != band_r) {  // Toeplitz bands of the normalised taps (uniform across the compute warps)
+        // Toeplitz bands of the plan's normalised taps, rebuilt whenever the tile's
+        // plan differs from the previous tile's (images of one radius r differ
+        // in sigma_s, so the taps, not r, identify the bands; uniform across the
+        // compute warps)
+        if (g.taps != band_taps) {
             for (int i = tid; i < g.Kw1 * 64; i += kComputeThreads) {
                 const int k = i >> 6, n = i & 63, u = k - n;
                 const uint16_t v = (u >= 0 && u <= 2 * r) ? g.taps[u] : (uint16_t)0;
@@ -475,7 +479,7 @@ __global__ void __launch_bounds__(kT, 1)
                 const uint16_t v = (u >= 0 && u <= 2 * r) ? g.taps[u] : (uint16_t)0;
                 *reinterpret_cast<uint16_t *>(B2 + ((k >> 3) * 2 + (n >> 3)) * 128 + (n & 7) * 16 + (k & 7) * 2) = v;
             }
-            band_r = r;
+            band_taps = g.taps;
         }
 
         // ---- region f -> tensor memory; in-image masks -------------------------------
