@@ -45,10 +45,11 @@ def algorithmic_flops_per_pixel(d: int, r: int, K: int) -> float:
 # only stands for the kernel source it was taken on (sha1 of that file): after
 # any change to the source the bench reports null until a new capture.
 MEASURED_TRAFFIC = {
-    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "72bbe6ac7b91740937590dcfe38310efcff2c38d",
-               "workload": "4k", "bytes_per_launch": 100.601e6 + 58.787e6,
+    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "44ec6a4a095d94ce9919aa5867e9563fea1e4a76",
+               "workload": "4k", "bytes_per_launch": 100.713e6 + 60.344e6,
                "capture": "ncu --set full --clock-control none -k regex:mcsf_tc -s 2 -c 1, one launch of "
-                          "bench.py --steps 2 --warmup 3 --variant fp16tc --no-cpu-baseline --no-fp32-compare"},
+                          "bench.py --steps 2 --warmup 3 --variant fp16tc --no-cpu-baseline --no-fp32-compare "
+                          "--no-extras --tune off"},
     "fp32rec": {"src": "paper_1605_02164_gb300/csrc/bf_recursive.cu", "sha1": "ae50e6fedcb753639417caa1d0166d124187c5a9",
                 "bytes_per_pixel_term": (1.966 + 3.941 + 7.515 + 3.207) * 1e9 / (64 * 1024 * 1024),
                 "capture": "ncu --set full --clock-control none of one row and one column launch (64 terms) of "
