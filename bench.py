@@ -441,18 +441,23 @@ def setup_tuning(args, groups):
             "key": "variant:d:ceil(r/8):size class:context (0 alone, 1 batch)", "tile_rows": chosen}
 
 
+def _on_tc(bf, d, variant):
+    """The tensor-core kernels take d = 3 and d = 6 images; others run on the FP32 kernel."""
+    return variant in (bf.BF_FP16TC, bf.BF_BF16TC) and d in (3, 6)
+
+
 def _split_items(bf, items_and_d, variant):
-    """Tensor-core launches take the d = 3 images; other d run on the FP32 kernel."""
-    tc = [it for it, d in items_and_d if d == 3 and variant != bf.BF_FP32]
-    fp = [it for it, d in items_and_d if not (d == 3 and variant != bf.BF_FP32)]
+    tc = [it for it, d in items_and_d if _on_tc(bf, d, variant)]
+    fp = [it for it, d in items_and_d if not _on_tc(bf, d, variant)]
     return tc, fp
 
 
 def batch_line(args):
     """Uneven batch: 64 images, sizes U[256, 2048] x U[256, 1536], d in {3, 6},
     sigma_s ~ U[2, 10], C with condition number <= 10, K in {32, 64, 128}.
-    One persistent launch (d = 3 on the tensor cores, d = 6 on the FP32
-    kernel) against one launch per image, and the plain FP32 path."""
+    One bf_filter_batch call on the tensor cores (a persistent launch for the
+    d = 3 images and one for the d = 6 images; with --variant fp32 every image
+    on the FP32 kernel) against one launch per image, and the plain FP32 path."""
     import torch
     from paper_1605_02164_gb300 import bf
     from paper_1605_02164_gb300 import build as B
@@ -481,7 +486,7 @@ def batch_line(args):
 
     def per_image(v):
         for it, d in items:
-            bf.bf_filter(*it, v if (d == 3 or v == bf.BF_FP32) else bf.BF_FP32, sp)
+            bf.bf_filter(*it, v if (_on_tc(bf, d, v) or v == bf.BF_FP32) else bf.BF_FP32, sp)
 
     def timed(fn, reps):
         fn()
@@ -496,7 +501,7 @@ def batch_line(args):
 
     keys = []
     for (it, d), w in zip(items, ws):
-        v = variant if (d == 3 and variant != bf.BF_FP32) else bf.BF_FP32
+        v = variant if _on_tc(bf, d, variant) else bf.BF_FP32
         keys.append((v, d, it[0].r, w.H, w.W, bf.BF_TUNE_BATCH))
     bf.bf_tune_clear()
     ms_untuned = timed(batched, args.steps)       # the kernels' cost models (tallest tiles)
@@ -508,7 +513,8 @@ def batch_line(args):
             "steps": args.steps, "ms_per_step": ms_batch, "higher_is_better": True, "dtype": args.variant,
             "data": "synthetic",
             "config": {"workload": f"batch{len(ws)}_sizes256-2048x256-1536_d3or6_s2-10_K32-128",
-                       "images": len(ws), "mpixel": px / 1e6, "d3_images": len(tc), "d6_images": len(fp)},
+                       "images": len(ws), "mpixel": px / 1e6, "d3_images": sum(w.d == 3 for w in ws), "d6_images": sum(w.d == 6 for w in ws),
+                       "tensor_core_images": len(tc), "fp32_images": len(fp)},
             "per_image_launches_mpx": px / ms_single / 1e3, "plain_fp32_mpx": px / ms_fp32 / 1e3,
             "images_per_s": len(ws) / ms_batch * 1e3, "untuned_mpx": px / ms_untuned / 1e3,
             "untuned_ms": ms_untuned, "tuning": tuning}

@@ -127,8 +127,12 @@ int bf_plan_destroy(bf_plan_t plan);
  *   H, W     image size; H == 0 or W == 0 is a no-op returning BF_OK.
  *   pitch    row stride in elements, pitch >= W and pitch % 4 == 0.
  *   variant  BF_FP32, BF_FP16TC, BF_BF16TC (windowed: r <= BF_MAX_RADIUS, else
- *            BF_ERR_UNSUPPORTED; the tensor-core variants need d = 3) or
- *            BF_FP32_RECURSIVE (any r; H <= 65535).
+ *            BF_ERR_UNSUPPORTED; the tensor-core variants need d = 3 or 6,
+ *            else BF_ERR_UNSUPPORTED) or BF_FP32_RECURSIVE (any r; H <= 65535).
+ *            With d = 6 the tensor-core kernel holds the image as 16-bit codes
+ *            of a per-image affine map of each channel (error <= (max - min) /
+ *            65535 of that channel, far below the FP16/BF16 channel rounding)
+ *            and runs each term as two 8-channel passes.
  * Pixels whose Re Z is exactly 0 come out as IEEE inf/nan; nothing is clamped.
  * BF_FP32_RECURSIVE runs two kernels per term over the whole image and keeps
  * 2 x 2(d+1) + (d+1) FP32 planes of scratch per call in library memory.
@@ -146,7 +150,9 @@ typedef struct {
 /*
  * bf_filter_batch -- filter n independent images (each with its own plan,
  * size, d, sigma_s and K).  Tensor-core variants: one persistent-kernel launch
- * that pops tiles of all images from a device work queue.  BF_FP32: one
+ * that pops tiles of all images from a device work queue (one for the d = 3
+ * images, then one for the d = 6 images, preceded by a small kernel that
+ * finds each six-channel image's per-channel range).  BF_FP32: one
  * launch per image, spread over 4 library-owned streams that are ordered
  * after the work already on `stream` and before anything queued on it later
  * (images run concurrently).  BF_FP32_RECURSIVE: one image after another on
@@ -169,13 +175,13 @@ int bf_filter_batch(const bf_item *items, int n, int variant, void *stream);
  * at start-up), where a foreign cudaMalloc can fail or fragment the pool, and
  * latency-critical loops that cannot absorb the device-wide synchronisation a
  * cudaMalloc or cudaFree may cause.  This entry point serves them: its
- * scratch is a file-scope device array of 26.25 KB (the control words plus
- * the table for BF_NOALLOC_MAX_ITEMS images) that every GPU loading the
+ * scratch is a file-scope device array of 40.25 KB (the control words plus
+ * the table and the six-channel range keys for BF_NOALLOC_MAX_ITEMS images) that every GPU loading the
  * library holds until the process exits.  It calls no cudaMalloc, cudaFree or
  * other allocating routine, on the device or the host.
  *   items, stream   as bf_filter_batch; the caller still owns every image.
  *   variant         BF_FP16TC or BF_BF16TC (else BF_ERR_ARG); every image
- *                   must have d = 3 (else BF_ERR_UNSUPPORTED).
+ *                   must have d = 3 or 6 (else BF_ERR_UNSUPPORTED).
  *   n               0..BF_NOALLOC_MAX_ITEMS; larger n returns BF_ERR_BUDGET
  *                   before any work is queued (split the batch).
  * Results are identical to bf_filter_batch with the same arguments.

@@ -51,6 +51,7 @@ static_assert(128 * kRegsIssuer + kComputeThreads * kRegsCompute <= kT * kRegsLa
 constexpr int kBX = 64;        // output columns per tile
 constexpr int kNC = 8;         // 16-row chunks per region (128 rows)
 constexpr int kNOC = 5;        // output chunks (of 16 rows) per tile at most
+constexpr int kNOC6 = 3;       // the same for six-channel images
 constexpr uint32_t kColF = 0;  // TMEM columns: region f (384), D1 (64), D2 (64)
 constexpr uint32_t kColD1 = 384;
 constexpr uint32_t kColD2 = 448;
@@ -93,9 +94,12 @@ struct TcImg {
     int Kw1, ks1;           // horizontal pass: 64 + 2r rounded up to 16, K-steps of 16
     int BY, nc, ringC;      // output rows per tile, 16-row chunks per term, centre-ring rows
     int tiles_x, tile_begin, ringA;  // ringA: rows of the blurred-row ring
-    int spec, pad;                   // spec: index + 1 into kSpecGeom, or 0 (general loop)
+    int spec, d;                     // spec: index + 1 into kSpecGeom, or 0 (general loop); d = 3 or 6
+    // d = 6: the image's per-channel range as order keys (minima at mm[0..5],
+    // maxima at mm[6 n_imgs + 0..5]), written by tc_range_kernel before the launch
+    uint32_t *mm;
 };
-static_assert(sizeof(TcImg) == 104, "descriptor layout");
+static_assert(sizeof(TcImg) == 112, "descriptor layout");
 
 // Shared-memory layout of a launch, sized for the largest window in it.
 struct TcLayout {
@@ -103,6 +107,7 @@ struct TcLayout {
     int fix;     // the specialised loop every image of the launch runs (kSpecGeom index + 1), or 0
     int spin;    // try_wait attempts before a wait on the tensor core gives up
     int inject;  // 1: skip the first MMA group of every tile (BF_FAULT_TC_WAIT), so the wait runs out
+    int d6;      // 1: the launch's images have six channels (the D6 kernel)
 };
 
 
@@ -205,6 +210,45 @@ __device__ __forceinline__ void tmem_st4(uint32_t a, const float *v) {
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld8u(uint32_t a, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void tmem_ld4u(uint32_t a, uint32_t *r) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(a));
+}
+
+__device__ __forceinline__ void tmem_st8u(uint32_t a, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(a), "r"(v[0]), "r"(v[1]),
+                 "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_st4u(uint32_t a, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(a), "r"(v[0]), "r"(v[1]), "r"(v[2]),
+                 "r"(v[3])
+                 : "memory");
+}
+
+// Six-channel region codes: a float's bits mapped to an unsigned key with the
+// same order (for the block-wide min / max), and the 16-bit affine code
+// f ~ lo + scale * code, decoded as (2^23 + code) * scale + (lo - 2^23 scale)
+// in one FMA (absolute error <= scale).
+__device__ __forceinline__ uint32_t order_key(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_unkey(uint32_t k) {
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+__device__ __forceinline__ float decode16(uint32_t code, float scale, float c0) {
+    return fmaf(__uint_as_float(0x4B000000u | code), scale, c0);
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t a, float *v) {
     uint32_t r[8];
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -286,11 +330,18 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // a 512 x 512 image) is 4 % faster than the dispatching one, while for loops 1,
 // 2, 3 and 6 the dispatching kernel is ~1 % faster (ptxas arranges the two
 // differently), so only FIX = 4 and 5 are built.
-template <bool BF16, int FIX>
+// D6 = true: the kernel for six-channel images.  Each term runs as two passes
+// of 8 channels in the layout of the three-channel kernel (cos f_1..f_4 and
+// sin f_1..f_4; then cos f_5, cos f_6, cos, 0 and sin f_5, sin f_6, sin, 0);
+// the region is held as 16-bit codes of a per-tile, per-channel affine map
+// (6 channels x 128 columns fit the same 384 TMEM columns), tiles are at most
+// 48 rows (two sets of accumulators), and every tile runs the general loop.
+template <bool BF16, int FIX, bool D6>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,
                    int *__restrict__ status, TcLayout lay) {
-    constexpr int NOC = kNOC;
+    constexpr int NOC = D6 ? kNOC6 : kNOC;
+    constexpr int NP = D6 ? 2 : 1;  // passes per term
     using P2 = Pair<BF16>;
     extern __shared__ __align__(1024) uint8_t sm[];
     // [0] horizontal MMAs done, [1] vertical MMAs done (4 issuers), [2..5]
@@ -298,6 +349,9 @@ __global__ void __launch_bounds__(kT, 1)
     __shared__ __align__(8) uint64_t mbar[6];
     __shared__ uint32_t taddr_s;
     __shared__ int tile_s, cstop_s;
+    // six-channel tiles: the image's minimum keys, then scale[0..5], -, -, c0[0..5], -, - of the affine codes
+    __shared__ uint32_t mm_s[6];
+    __shared__ __align__(16) float aff_s[16];
 
     uint8_t *A1 = sm;               // 2 x [mg 16][kg 16][8 rows][16 B]   K-major (double buffer)
     uint8_t *A2 = sm + lay.offA2;   // [kg ringA/8][tile 4][mg 16][8][16 B]  MN-major ring of blurred rows
@@ -355,7 +409,7 @@ __global__ void __launch_bounds__(kT, 1)
             while (im + 1 < n_imgs && __ldg(&imgs[im + 1].tile_begin) <= tile) ++im;
             const TcImg &gg = imgs[im];
             const int K = gg.K, NCr = gg.nc, lag = gg.lag, BY = gg.BY;
-            const int S = K * NCr;
+            const int S = NP * K * NCr;
             // ---- MMA issue --------------------------------------------------------------
             const int ks1 = gg.ks1, ksteps = gg.ksteps, kgring = gg.ringA >> 3;
             const uint64_t dA1 = sdesc(smem_u32(A1), 128, 2048);  // K-major: LBO = next K group, SBO = next 8 rows
@@ -453,7 +507,8 @@ __global__ void __launch_bounds__(kT, 1)
         while (im + 1 < n_imgs && __ldg(&imgs[im + 1].tile_begin) <= tile) ++im;
         const TcImg g = imgs[im];
         const int K = g.K, NCr = g.nc, lag = g.lag, BY = g.BY;
-        const int S = K * NCr;
+        const int KP = NP * K;  // "terms" of the step sequence: passes
+        const int S = KP * NCr;
         const float *__restrict__ in = g.in;
         float *__restrict__ out = g.out;
         const float *__restrict__ nu_hi = g.nu_hi;
@@ -493,6 +548,64 @@ __global__ void __launch_bounds__(kT, 1)
             const int cx = 8 * xg + px0 + jj - r;
             if (cx >= 0 && cx < kBX) cmask |= 1u << jj;
         }
+        if constexpr (D6) {
+            // Six channels as 16-bit codes of an affine map per image and channel,
+            // spanning the image's values (f ~ lo + scale code, scale = (max - min)
+            // / 65535; the same map for every tile, so results do not depend on
+            // the tiling): 4 pixels x 6 channels = 12 words per
+            // thread and chunk, words 0-7 at columns 8 gi .. 8 gi + 7 and words
+            // 8-11 at 256 + 4 gi .. + 3, gi = 2 (2c + h) + e; word 2 ch + p holds
+            // pixels 2p, 2p + 1 of channel ch.
+            for (int c = 0; c < kNC; ++c) {
+                const int gy = ry0 + 16 * c + row;
+                const bool rowv = gy >= 0 && gy < H;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    const int gx = rx0 + 8 * xg + px0 + jj;
+                    if (rowv && gx >= 0 && gx < W) vmask |= 1u << (4 * c + jj);
+                }
+            }
+            if (tid == 0) {
+                for (int ch = 0; ch < 6; ++ch) {
+                    float lo = order_unkey(__ldcg(g.mm + ch)), hi = order_unkey(__ldcg(g.mm + 6 * n_imgs + ch));
+                    if (!(hi >= lo)) lo = hi = 0.f;  // no in-image value (cannot happen for a non-empty image)
+                    const float scale = (hi - lo) * (1.f / 65535.f);
+                    mm_s[ch] = order_key(lo);
+                    aff_s[ch] = scale;
+                    aff_s[8 + ch] = fmaf(-8388608.f, scale, lo);
+                }
+            }
+            compute_sync_or(false);
+            float lo6[6], inv6[6];
+#pragma unroll
+            for (int ch = 0; ch < 6; ++ch) {
+                const float scale = aff_s[ch];
+                lo6[ch] = order_unkey(mm_s[ch]);
+                inv6[ch] = scale > 0.f ? 1.f / scale : 0.f;
+            }
+            for (int c = 0; c < kNC; ++c) {
+                uint32_t wd[12];
+#pragma unroll
+                for (int ch = 0; ch < 6; ++ch) {
+                    uint32_t code[4];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const long long gy = ry0 + 16 * c + row, gx = rx0 + 8 * xg + px0 + jj;
+                        float q16 = 0.f;
+                        if (((vmask >> (4 * c + jj)) & 1) && dcheck(gy >= 0 && gy < H && gx >= 0 && gx < W, status))
+                            q16 = rintf((__ldg(in + ch * plane + (size_t)gy * pitch + gx) - lo6[ch]) * inv6[ch]);
+                        code[jj] = (uint32_t)fminf(fmaxf(q16, 0.f), 65535.f);
+                    }
+                    wd[2 * ch] = code[0] | (code[1] << 16);
+                    wd[2 * ch + 1] = code[2] | (code[3] << 16);
+                }
+                const int gi = 2 * (2 * c + h) + e;
+                if (dcheck(8 * gi + 8 <= 256 && 256 + 4 * gi + 4 <= (int)kColD1, status)) {
+                    tmem_st8u(tmem + lane_base + kColF + 8 * gi, wd);
+                    tmem_st4u(tmem + lane_base + kColF + 256 + 4 * gi, wd + 8);
+                }
+            }
+        } else
         for (int c = 0; c < kNC; ++c) {
             const int gy = ry0 + 16 * c + row;
             const bool rowv = gy >= 0 && gy < H;
@@ -528,13 +641,28 @@ __global__ void __launch_bounds__(kT, 1)
         // only through (row - r) & 7, a constant of the tile.
         const int rx = ring_xor((row - r) & 7), cb = 8 * xg + px0 - r;
         const int rcol0 = cb ^ rx, rcol1 = (cb + 1) ^ rx, rcol2 = (cb + 2) ^ rx, rcol3 = (cb + 3) ^ rx;
-        float nr0, nr1, nr2;  // frequency of the current term, turns per unit of f
+        float nr0, nr1, nr2, nr3 = 0.f, nr4 = 0.f, nr5 = 0.f;  // frequency of the current term, turns per unit of f
         auto load_nu = [&](int k) {
-            nr0 = __ldg(nu_hi + 3 * k);
-            nr1 = __ldg(nu_hi + 3 * k + 1);
-            nr2 = __ldg(nu_hi + 3 * k + 2);
+            if constexpr (D6) {
+                nr0 = __ldg(nu_hi + 6 * k);
+                nr1 = __ldg(nu_hi + 6 * k + 1);
+                nr2 = __ldg(nu_hi + 6 * k + 2);
+                nr3 = __ldg(nu_hi + 6 * k + 3);
+                nr4 = __ldg(nu_hi + 6 * k + 4);
+                nr5 = __ldg(nu_hi + 6 * k + 5);
+            } else {
+                nr0 = __ldg(nu_hi + 3 * k);
+                nr1 = __ldg(nu_hi + 3 * k + 1);
+                nr2 = __ldg(nu_hi + 3 * k + 2);
+            }
         };
-        int pend_oc = -1, pend_slot = 0;
+        int pend_oc = -1, pend_slot = 0, pend_pass = 0;
+        // second set of accumulators of a six-channel tile (the pass-2 channels f_5, f_6, 1)
+        float acc1[D6 ? NOC : 1][8];
+#pragma unroll
+        for (int o = 0; o < (D6 ? NOC : 1); ++o)
+#pragma unroll
+            for (int j = 0; j < 8; ++j) acc1[o][j] = 0.f;
 
         // A: channels of flat step s (chunk c of the term whose frequency is in
         // nr0..nr2) into A1[s & 1]; slot16 = 16 s mod ringC.
@@ -612,9 +740,102 @@ __global__ void __launch_bounds__(kT, 1)
             }
         };
 
+        // A for a six-channel tile: pass 0 builds cos f_1..f_4, sin f_1..f_4, pass
+        // 1 cos f_5, cos f_6, cos, 0, sin f_5, sin f_6, sin, 0, in the channel
+        // slots of the three-channel layout; the phase uses all six channels.
+        auto stage_A6 = [&](int s, int c, int slot16, int pass) {
+            float fv[6][4];
+            {
+                uint32_t wd[12];
+                const int gi = 2 * (2 * c + h) + e;
+                tmem_ld8u(tmem + lane_base + kColF + 8 * gi, wd);
+                tmem_ld4u(tmem + lane_base + kColF + 256 + 4 * gi, wd + 8);
+                tmem_wait_ld();
+                const float4 sc0 = *reinterpret_cast<const float4 *>(aff_s);
+                const float4 sc1 = *reinterpret_cast<const float4 *>(aff_s + 4);
+                const float4 cc0 = *reinterpret_cast<const float4 *>(aff_s + 8);
+                const float4 cc1 = *reinterpret_cast<const float4 *>(aff_s + 12);
+                const float scl[6] = {sc0.x, sc0.y, sc0.z, sc0.w, sc1.x, sc1.y};
+                const float cst[6] = {cc0.x, cc0.y, cc0.z, cc0.w, cc1.x, cc1.y};
+#pragma unroll
+                for (int ch = 0; ch < 6; ++ch) {
+#pragma unroll
+                    for (int p = 0; p < 2; ++p) {
+                        const uint32_t w2 = wd[2 * ch + p];
+                        fv[ch][2 * p] = decode16(w2 & 0xFFFFu, scl[ch], cst[ch]);
+                        fv[ch][2 * p + 1] = decode16(w2 >> 16, scl[ch], cst[ch]);
+                    }
+                }
+            }
+            const uint32_t vm = (vmask >> (4 * c)) & 0xFu;
+            const int ry = 16 * c + row;
+            const bool centre_row = ry >= r && ry < r + BY && cmask;
+            uint32_t o[8][2];
+            float csv[4], snv[4];
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                float cv[2], sv[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int j = 2 * p + u;
+                    // phase in turns, reduced to [-1/2, 1/2] before the SFU sin/cos (Eq. Ht)
+                    float tt = fmaf(nr0, fv[0][j], fmaf(nr1, fv[1][j], fmaf(nr2, fv[2][j],
+                                    fmaf(nr3, fv[3][j], fmaf(nr4, fv[4][j], nr5 * fv[5][j])))));
+                    tt -= rintf(tt);
+                    float s_, c_;
+                    __sincosf(6.28318530717958647692f * tt, &s_, &c_);
+                    const bool v = (vm >> j) & 1u;
+                    cv[u] = v ? c_ : 0.f;
+                    sv[u] = v ? s_ : 0.f;
+                    csv[j] = cv[u];
+                    snv[j] = sv[u];
+                }
+                const typename P2::T hc = P2::make(cv[0], cv[1]);
+                const typename P2::T hs = P2::make(sv[0], sv[1]);
+                // channel q of the pass: f_{q+1} (pass 0), f_5, f_6, 1, 0 (pass 1)
+                auto prod = [&](int ch, float t0, float t1, typename P2::T ht) -> uint32_t {
+                    if constexpr (BF16)
+                        return bits(P2::make(t0 * fv[ch][2 * p], t1 * fv[ch][2 * p + 1]));
+                    else
+                        return bits(__hmul2(ht, P2::make(fv[ch][2 * p], fv[ch][2 * p + 1])));
+                };
+                if (pass == 0) {
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        o[q4][p] = prod(q4, cv[0], cv[1], hc);
+                        o[4 + q4][p] = prod(q4, sv[0], sv[1], hs);
+                    }
+                } else {
+                    o[0][p] = prod(4, cv[0], cv[1], hc);
+                    o[1][p] = prod(5, cv[0], cv[1], hc);
+                    o[2][p] = bits(hc);
+                    o[3][p] = 0u;
+                    o[4][p] = prod(4, sv[0], sv[1], hs);
+                    o[5][p] = prod(5, sv[0], sv[1], hs);
+                    o[6][p] = bits(hs);
+                    o[7][p] = 0u;
+                }
+            }
+            if (centre_row && dcheck(slot16 + row - r >= -g.ringC && slot16 + row - r < g.ringC, status)) {
+                int slot = slot16 + row - r;
+                if (slot < 0) slot += g.ringC;
+                float2 *rrow = ring + slot * kBX;
+                if (cmask & 1u) rrow[rcol0] = make_float2(csv[0], snv[0]);
+                if (cmask & 2u) rrow[rcol1] = make_float2(csv[1], snv[1]);
+                if (cmask & 4u) rrow[rcol2] = make_float2(csv[2], snv[2]);
+                if (cmask & 8u) rrow[rcol3] = make_float2(csv[3], snv[3]);
+            }
+            uint8_t *dst = dstA + (s & 1) * 32768;
+            if (dcheck(dst >= A1 && dst + 7 * 4096 + 8 <= A1 + 65536, status)) {
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch)
+                    *reinterpret_cast<uint2 *>(dst + ch * 4096) = make_uint2(o[ch][0], o[ch][1]);
+            }
+        };
+
         // C: combine output chunk oc; slot0 = ring row of its output row 16 oc + 8 e
         // (a multiple of 8 at most ringC - 8: the 8 rows read never wrap)
-        auto stage_C = [&](int oc, int slot0) {
+        auto stage_C = [&](int oc, int slot0, int pass = 0) {
             if (!dcheck(slot0 >= 0 && slot0 + 8 <= g.ringC && oc >= 0 && oc < NOC, status)) return;
             float vc[8], vs[8];  // output rows 16 oc + 8 e + j of the cos / sin M-tile
             tmem_ld8(tmem + lane_base + kColD2 + 16 * (2 * h) + 8 * e, vc);
@@ -625,10 +846,18 @@ __global__ void __launch_bounds__(kT, 1)
 #pragma unroll
             for (int o = 0; o < NOC; ++o) {
                 if (o == oc) {
+                    if (D6 && pass) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const float2 cs = rrow[j * kBX + (x ^ ring_xor(j))];
-                        acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 cs = rrow[j * kBX + (x ^ ring_xor(j))];
+                            acc1[D6 ? o : 0][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc1[D6 ? o : 0][j]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 cs = rrow[j * kBX + (x ^ ring_xor(j))];
+                            acc[o][j] = fmaf(cs.x, vc[j], fmaf(cs.y, vs[j], acc[o][j]));
+                        }
                     }
                 }
             }
@@ -668,7 +897,10 @@ __global__ void __launch_bounds__(kT, 1)
 
         // ---- prologue ------------------------------------------------------------------
         load_nu(0);
-        stage_A(0, 0, 0);
+        if constexpr (D6)
+            stage_A6(0, 0, 0, 0);
+        else
+            stage_A(0, 0, 0);
         if (!step_done()) goto cmp_tile_end;
 
         {
@@ -740,23 +972,36 @@ __global__ void __launch_bounds__(kT, 1)
                 // Step s is chunk c of term k; slotS = 16 s mod ringC and krS = 16 s mod Kw
                 // are carried from step to step (no division in the loop), as are the
                 // chunk, term and slot of step s + 1 (cA, kA, slotA).
+                // A six-channel tile runs 2K passes ("terms" kA of the sequence);
+                // pass kA & 1 of term kA >> 1.
                 {
                     int c = 0, kA = 0, cA = 0, slotS = 0, krS = 0;
                     for (int s = 0; s < S; ++s) {
                         const int oc = c - lag;
                         const bool do_m2 = oc >= 0 && oc < NOC && 16 * oc < BY;
+                        const int passS = D6 ? (kA & 1) : 0;  // pass of step s
                         if (++cA == NCr) {
                             cA = 0;
-                            if (++kA < K) load_nu(kA);
+                            if (++kA < KP) {
+                                if (!D6)
+                                    load_nu(kA);
+                                else if ((kA & 1) == 0)
+                                    load_nu(kA >> 1);
+                            }
                         }
                         int slotA = slotS + 16;
                         if (slotA >= g.ringC) slotA -= g.ringC;
-                        if (s + 1 < S) stage_A(s + 1, cA, slotA);
+                        if (s + 1 < S) {
+                            if constexpr (D6)
+                                stage_A6(s + 1, cA, slotA, kA & 1);
+                            else
+                                stage_A(s + 1, cA, slotA);
+                        }
                         if (pend_oc >= 0) {
                             if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                             ph2 ^= 1;
                             fence_after();
-                            stage_C(pend_oc, pend_slot);
+                            stage_C(pend_oc, pend_slot, pend_pass);
                             pend_oc = -1;
                         }
                         if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
@@ -766,6 +1011,7 @@ __global__ void __launch_bounds__(kT, 1)
                         if (!step_done()) return false;
                         if (do_m2) {
                             pend_oc = oc;
+                            pend_pass = passS;
                             // flat output row 16 (s - lag) + 8 e, mod ringC (16 lag < ringC)
                             int sl = slotS - 16 * lag + 8 * e;
                             if (sl < 0) sl += g.ringC;
@@ -782,12 +1028,13 @@ __global__ void __launch_bounds__(kT, 1)
                     if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                     ph2 ^= 1;
                     fence_after();
-                    stage_C(pend_oc, pend_slot);
+                    stage_C(pend_oc, pend_slot, pend_pass);
                 }
                 return true;
             };
             bool go;
-            switch (FIX ? FIX : g.spec) {
+            if constexpr (D6) go = general_loop();
+            else switch (FIX ? FIX : g.spec) {
                 case 1: go = spec_loop(IC<6>(), IC<1>(), IC<5>(), IC<1>()); break;
                 case 2: go = spec_loop(IC<7>(), IC<2>(), IC<5>(), IC<1>()); break;
                 case 3: go = spec_loop(IC<8>(), IC<3>(), IC<5>(), IC<1>()); break;
@@ -808,24 +1055,30 @@ __global__ void __launch_bounds__(kT, 1)
         {
             float *zbuf = reinterpret_cast<float *>(sm + lay.offC);  // [BY][64], reuses the centre ring
             const int x = 32 * h + l;
-            if (q == 3) {
+            // Z: channel 3 of the (only) pass, or channel 2 of a six-channel tile's second pass
+            if (q == (D6 ? 2 : 3)) {
 #pragma unroll
                 for (int o = 0; o < NOC; ++o)
 #pragma unroll
                     for (int j = 0; j < 8; ++j)
                         if (16 * o + 8 * e + j < BY && dcheck((16 * o + 8 * e + j + 1) * kBX * 4 <= (int)(lay.smem - lay.offC), status))
-                            zbuf[(16 * o + 8 * e + j) * kBX + x] = acc[o][j];
+                            zbuf[(16 * o + 8 * e + j) * kBX + x] = D6 ? acc1[D6 ? o : 0][j] : acc[o][j];
             }
             __syncthreads();  // z buffer
             const int gx = tx0 + x;
-            if (q < 3 && gx < W) {
+            // P_{q+1} from the first pass's channel q; a six-channel tile's P_5, P_6
+            // from the second pass's channels 0, 1
+            if (q < (D6 ? 4 : 3) && gx < W) {
 #pragma unroll
                 for (int o = 0; o < NOC; ++o)
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         const int y = 16 * o + 8 * e + j, gy = ty0 + y;
-                        if (y < BY && gy < H && dcheck(gy >= 0 && gx >= 0 && gx < W, status))
-                            out[q * plane + (size_t)gy * pitch + gx] = acc[o][j] / zbuf[y * kBX + x];
+                        if (y < BY && gy < H && dcheck(gy >= 0 && gx >= 0 && gx < W, status)) {
+                            const float zi = zbuf[y * kBX + x];
+                            out[q * plane + (size_t)gy * pitch + gx] = acc[o][j] / zi;
+                            if (D6 && q < 2) out[(4 + q) * plane + (size_t)gy * pitch + gx] = acc1[D6 ? o : 0][j] / zi;
+                        }
                     }
             }
         }
@@ -862,7 +1115,7 @@ bool tc_geometry(int r, TcImg &g) {
     if (g.Kw1 > 128 || g.ksteps > 5) return false;
     int noc = (128 - 2 * r) / 16;
     if (noc > kNC - g.lag) noc = kNC - g.lag;
-    if (noc > kNOC) noc = kNOC;
+    if (noc > (g.d == 6 ? kNOC6 : kNOC)) noc = g.d == 6 ? kNOC6 : kNOC;
     if (noc < 1) return false;
     g.BY = 16 * noc;
     g.nc = cdiv(g.BY + 2 * r, 16);
@@ -883,6 +1136,7 @@ TcLayout tc_layout(int max_ringA, int max_Kw, int max_Kw1, int max_ringC, int ma
     L.fix = 0;
     L.spin = kSpinLimit;
     L.inject = 0;
+    L.d6 = 0;
     return L;
 }
 
@@ -892,15 +1146,68 @@ TcLayout tc_layout(int max_ringA, int max_Kw, int max_Kw1, int max_ringC, int ma
 // the dynamic queue ends on cheap tiles), copies it with zeroed control words
 // into `scratch`, and launches one persistent grid.  `scratch` must hold
 // tc_scratch_bytes(n) bytes and is owned by the caller for the stream.
-size_t tc_scratch_bytes(int n) { return (size_t)kCtrlWords * sizeof(int) + (size_t)n * sizeof(TcImg); }
+size_t tc_scratch_bytes(int n) {
+    return (size_t)kCtrlWords * sizeof(int) + (size_t)n * (sizeof(TcImg) + 12 * sizeof(uint32_t));
+}
 
 namespace {
+
+// Per-channel range of every six-channel image of a launch (the affine map of
+// its 16-bit region codes), as order keys: block-wide min / max of the rows
+// the block takes, then one atomic per warp.  The keys start at 0xFFFFFFFF
+// (minima) and 0 (maxima).
+__global__ void __launch_bounds__(256) tc_range_kernel(const TcImg *__restrict__ imgs, int m) {
+    const TcImg &g = imgs[blockIdx.y];
+    const size_t plane = (size_t)g.H * g.pitch;
+    float mn[6], mx[6];
+#pragma unroll
+    for (int ch = 0; ch < 6; ++ch) {
+        mn[ch] = __int_as_float(0x7F800000);
+        mx[ch] = -mn[ch];
+    }
+    for (int y = blockIdx.x; y < g.H; y += gridDim.x)
+        for (int x = threadIdx.x; x < g.W; x += blockDim.x)
+#pragma unroll
+            for (int ch = 0; ch < 6; ++ch) {
+                const float v = __ldg(g.in + ch * plane + (size_t)y * g.pitch + x);
+                mn[ch] = fminf(mn[ch], v);
+                mx[ch] = fmaxf(mx[ch], v);
+            }
+#pragma unroll
+    for (int ch = 0; ch < 6; ++ch) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[ch] = fminf(mn[ch], __shfl_xor_sync(0xFFFFFFFFu, mn[ch], o));
+            mx[ch] = fmaxf(mx[ch], __shfl_xor_sync(0xFFFFFFFFu, mx[ch], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int ch = 0; ch < 6; ++ch) {
+            atomicMin(g.mm + ch, order_key(mn[ch]));
+            atomicMax(g.mm + 6 * m + ch, order_key(mx[ch]));
+        }
+    }
+}
+
+// Range keys of a six-channel table at `keys` (6 m minima, then 6 m maxima):
+// set the starting values and launch tc_range_kernel.
+int tc_ranges(const TcImg *imgs_dev, uint32_t *keys, int m, cudaStream_t s) {
+    if (cudaMemsetAsync(keys, 0xFF, (size_t)6 * m * sizeof(uint32_t), s) != cudaSuccess ||
+        cudaMemsetAsync(keys + 6 * m, 0, (size_t)6 * m * sizeof(uint32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return BF_ERR_CUDA;
+    }
+    tc_range_kernel<<<dim3(64, m), 256, 0, s>>>(imgs_dev, m);
+    return cuda_err(cudaGetLastError());
+}
 
 // Descriptor of one image (tile_begin left 0); false if the tile scheme cannot hold it.
 int tc_fill(const bf_item &it, int variant, TcImg &g) {
     const bf_plan_s &p = *it.plan;
-    if (p.d != 3) return BF_ERR_UNSUPPORTED;
+    if (p.d != 3 && p.d != 6) return BF_ERR_UNSUPPORTED;
     g = TcImg{};
+    g.d = p.d;
     if (!tc_geometry(p.r, g)) return BF_ERR_UNSUPPORTED;
     g.in = it.in;
     g.out = it.out;
@@ -974,7 +1281,7 @@ void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
     const long long ring_rows = ((long long)max_smem - 1024 - (long long)base.offC) / (kBX * 8);
     for (int i = 0; i < m; ++i) {
         tab[i].spec = 0;
-        for (int j = 0; j < kNumSpec; ++j) {
+        for (int j = 0; j < kNumSpec && tab[i].d == 3; ++j) {
             const int rows = 16 * kSpecGeom[j].nc * kSpecGeom[j].terms;
             if (tab[i].nc == kSpecGeom[j].nc && tab[i].lag == kSpecGeom[j].lag && tab[i].BY == kSpecGeom[j].BY &&
                 rows <= ring_rows) {
@@ -1009,11 +1316,15 @@ int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *statu
     using Kern = void (*)(const TcImg *, int, int, int *, int *, TcLayout);
     Kern kern;
     const bool b = variant == BF_BF16TC;
-    switch (lay.fix) {
-        case 0: kern = b ? mcsf_tc_kernel<true, 0> : mcsf_tc_kernel<false, 0>; break;
-        case 4: kern = b ? mcsf_tc_kernel<true, 4> : mcsf_tc_kernel<false, 4>; break;
-        case 5: kern = b ? mcsf_tc_kernel<true, 5> : mcsf_tc_kernel<false, 5>; break;
-        default: return BF_ERR_ARG;
+    if (lay.d6) {
+        kern = b ? mcsf_tc_kernel<true, 0, true> : mcsf_tc_kernel<false, 0, true>;
+    } else {
+        switch (lay.fix) {
+            case 0: kern = b ? mcsf_tc_kernel<true, 0, false> : mcsf_tc_kernel<false, 0, false>; break;
+            case 4: kern = b ? mcsf_tc_kernel<true, 4, false> : mcsf_tc_kernel<false, 4, false>; break;
+            case 5: kern = b ? mcsf_tc_kernel<true, 5, false> : mcsf_tc_kernel<false, 5, false>; break;
+            default: return BF_ERR_ARG;
+        }
     }
     // The register split inside the kernel assumes the launch gives each thread
     // kRegsLaunch registers; with fewer the compute warps' request could not be met.
@@ -1032,18 +1343,23 @@ int tc_launch(const TcImg *imgs_dev, int m, int total, int *ctrl_dev, int *statu
 }
 
 bool cost_before(const TcImg &a, const TcImg &b) {
-    const long long ca = (long long)a.K * a.nc, cb = (long long)b.K * b.nc;
+    const long long ca = (long long)a.K * a.nc * (a.d == 6 ? 2 : 1), cb = (long long)b.K * b.nc * (b.d == 6 ? 2 : 1);
     if (ca != cb) return ca > cb;
     return a.r < b.r;
 }
 
-// Fills, orders and finishes the table of a call; shared by both batch entry
-// points so that they launch identical work (a lone image gets its fitted
-// tile height in both).  m = number of non-empty images.
-int tc_prepare(const bf_item *items, int n, int variant, TcImg *tab, int *m_out, int *total, TcLayout *lay) {
+// Fills, orders and finishes the table of the call's images with d_sel
+// channels (3 or 6: one launch each); shared by both batch entry points so
+// that they launch identical work (a lone image gets its fitted tile height
+// in both).  m = number of non-empty images taken.
+int tc_prepare(const bf_item *items, int n, int variant, int d_sel, TcImg *tab, int *m_out, int *total,
+               TcLayout *lay) {
     int m = 0;
     for (int i = 0; i < n; ++i) {
         if (items[i].H == 0 || items[i].W == 0) continue;
+        const int d = items[i].plan->d;
+        if (d != 3 && d != 6) return BF_ERR_UNSUPPORTED;
+        if (d != d_sel) continue;
         const int rc = tc_fill(items[i], variant, tab[m]);
         if (rc != BF_OK) return rc;
         ++m;
@@ -1054,7 +1370,7 @@ int tc_prepare(const bf_item *items, int n, int variant, TcImg *tab, int *m_out,
     // (tc_fit_waves alone; the geometry's tallest tile in a batch)
     const int ctx = m == 1 ? BF_TUNE_ALONE : BF_TUNE_BATCH;
     for (int i = 0; i < m; ++i) {
-        const int rows = tune_rows(variant, 3, tab[i].r, tab[i].H, tab[i].W, ctx);
+        const int rows = tune_rows(variant, d_sel, tab[i].r, tab[i].H, tab[i].W, ctx);
         if (rows > 0)
             tc_set_noc(tab[i], rows / 16, tab[i].BY / 16);
         else if (m == 1)
@@ -1070,6 +1386,7 @@ int tc_prepare(const bf_item *items, int n, int variant, TcImg *tab, int *m_out,
         tab[b + 1] = t;
     }
     tc_finish(tab, m, total, lay);
+    lay->d6 = d_sel == 6;
     return BF_OK;
 }
 
@@ -1077,20 +1394,30 @@ int tc_prepare(const bf_item *items, int n, int variant, TcImg *tab, int *m_out,
 
 int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int *status, cudaStream_t s) {
     if (n <= 0) return BF_OK;
-    std::vector<unsigned char> host(tc_scratch_bytes(n), 0);  // control words (zero) + table
-    TcImg *tab = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
-    int m = 0, total = 0;
-    TcLayout lay{};
-    const int rc = tc_prepare(items, n, variant, tab, &m, &total, &lay);
-    if (rc != BF_OK || m == 0) return rc;
-    const size_t bytes = (size_t)kCtrlWords * sizeof(int) + (size_t)m * sizeof(TcImg);
-    if (cudaMemcpyAsync(scratch, host.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaGetLastError();
-        return BF_ERR_CUDA;
+    // One persistent launch for the three-channel images, then one for the
+    // six-channel ones, in stream order through the same scratch.
+    for (const int d_sel : {3, 6}) {
+        std::vector<unsigned char> host(tc_scratch_bytes(n), 0);  // control words (zero) + table
+        TcImg *tab = reinterpret_cast<TcImg *>(host.data() + kCtrlWords * sizeof(int));
+        int m = 0, total = 0;
+        TcLayout lay{};
+        int rc = tc_prepare(items, n, variant, d_sel, tab, &m, &total, &lay);
+        if (rc != BF_OK) return rc;
+        if (m == 0) continue;
+        const size_t bytes = (size_t)kCtrlWords * sizeof(int) + (size_t)m * sizeof(TcImg);
+        uint32_t *keys = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(scratch) + bytes);
+        for (int i = 0; i < m; ++i) tab[i].mm = d_sel == 6 ? keys + 6 * i : nullptr;
+        if (cudaMemcpyAsync(scratch, host.data(), bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return BF_ERR_CUDA;
+        }
+        int *ctrl = reinterpret_cast<int *>(scratch);
+        const TcImg *imgs = reinterpret_cast<const TcImg *>(reinterpret_cast<char *>(scratch) + kCtrlWords * sizeof(int));
+        if (d_sel == 6 && (rc = tc_ranges(imgs, keys, m, s)) != BF_OK) return rc;
+        rc = tc_launch(imgs, m, total, ctrl, status, lay, variant, s);
+        if (rc != BF_OK) return rc;
     }
-    int *ctrl = reinterpret_cast<int *>(scratch);
-    const TcImg *imgs = reinterpret_cast<const TcImg *>(reinterpret_cast<char *>(scratch) + kCtrlWords * sizeof(int));
-    return tc_launch(imgs, m, total, ctrl, status, lay, variant, s);
+    return BF_OK;
 }
 
 // ---------------------------------------------------------------------------------
@@ -1100,7 +1427,8 @@ int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int
 // Scratch of bf_filter_batch_noalloc: control words (tile counter, status)
 // followed by the image table for at most BF_NOALLOC_MAX_ITEMS images.  Every
 // GPU that loads the library holds these 26.25 KB until the process exits.
-constexpr size_t kNoAllocBytes = (size_t)kCtrlWords * sizeof(int) + (size_t)BF_NOALLOC_MAX_ITEMS * sizeof(TcImg);
+constexpr size_t kNoAllocBytes =
+    (size_t)kCtrlWords * sizeof(int) + (size_t)BF_NOALLOC_MAX_ITEMS * (sizeof(TcImg) + 12 * sizeof(uint32_t));
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 namespace {
@@ -1168,23 +1496,31 @@ extern "C" int bf_filter_batch_noalloc(const bf_item *items, int n, int variant,
         if (rc != BF_OK) return rc;
     }
     TcImg tab[BF_NOALLOC_MAX_ITEMS];  // host staging on the stack: no heap allocation either
-    int m = 0, total = 0;
-    TcLayout lay{};
-    const int rc = tc_prepare(items, n, variant, tab, &m, &total, &lay);
-    if (rc != BF_OK || m == 0) return rc;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BF_ERR_CUDA;
     char *scr = reinterpret_cast<char *>(noalloc_scratch(dev));
     if (!scr) return BF_ERR_CUDA;
     int *ctrl = reinterpret_cast<int *>(scr);
     TcImg *imgs = reinterpret_cast<TcImg *>(scr + kCtrlWords * sizeof(int));
-    const int zero = 0;  // the tile counter must start at zero; the status word is left as is
-    if (cudaMemcpyAsync(ctrl, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
-        cudaMemcpyAsync(imgs, tab, (size_t)m * sizeof(TcImg), cudaMemcpyHostToDevice, s) != cudaSuccess) {
-        cudaGetLastError();
-        return BF_ERR_CUDA;
+    for (const int d_sel : {3, 6}) {  // as bf_filter_batch: one launch per channel count, in stream order
+        int m = 0, total = 0;
+        TcLayout lay{};
+        int rc = tc_prepare(items, n, variant, d_sel, tab, &m, &total, &lay);
+        if (rc != BF_OK) return rc;
+        if (m == 0) continue;
+        uint32_t *keys = reinterpret_cast<uint32_t *>(imgs + m);
+        for (int i = 0; i < m; ++i) tab[i].mm = d_sel == 6 ? keys + 6 * i : nullptr;
+        const int zero = 0;  // the tile counter must start at zero; the status word is left as is
+        if (cudaMemcpyAsync(ctrl, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaMemcpyAsync(imgs, tab, (size_t)m * sizeof(TcImg), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+            cudaGetLastError();
+            return BF_ERR_CUDA;
+        }
+        if (d_sel == 6 && (rc = tc_ranges(imgs, keys, m, s)) != BF_OK) return rc;
+        rc = tc_launch(imgs, m, total, ctrl, ctrl + 1, lay, variant, s);
+        if (rc != BF_OK) return rc;
     }
-    return tc_launch(imgs, m, total, ctrl, ctrl + 1, lay, variant, s);
+    return BF_OK;
 }
 
 namespace bf {

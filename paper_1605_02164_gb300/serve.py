@@ -207,8 +207,8 @@ class Server:
     def _variant_of(self, r: Request, d: int) -> int:
         if r.variant is not None:
             return r.variant
-        if self.variant in (bf.BF_FP16TC, bf.BF_BF16TC) and d != 3:
-            return bf.BF_FP32  # the tensor-core kernel is for RGB
+        if self.variant in (bf.BF_FP16TC, bf.BF_BF16TC) and d not in (3, 6):
+            return bf.BF_FP32  # the tensor-core kernels hold three or six channels
         return self.variant
 
     def _launch(self, i: int, batch: list[Request]):

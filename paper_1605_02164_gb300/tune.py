@@ -38,8 +38,10 @@ def tc_max_rows(r: int) -> int:
     return 16 * max(1, min((128 - 2 * r) // 16, 8 - lag, 5))
 
 
-def candidates(variant: int, r: int, H: int) -> list[int]:
+def candidates(variant: int, r: int, H: int, d: int = 3) -> list[int]:
     top = tc_max_rows(r) if variant in (bf.BF_FP16TC, bf.BF_BF16TC) else 128
+    if variant in (bf.BF_FP16TC, bf.BF_BF16TC) and d == 6:
+        top = min(top, 48)  # two sets of accumulators: at most 3 output chunks
     top = min(top, 16 * (-(-H // 16)))  # no taller than the image needs
     return list(range(16, top + 1, 16))
 
@@ -100,7 +102,7 @@ def tune(variant: int, d: int, r: int, H: int, W: int, context: int = bf.BF_TUNE
     prev = bf.bf_tune_get(variant, d, r, cls, context)
     timings = {}
     try:
-        for rows in candidates(variant, r, H):
+        for rows in candidates(variant, r, H, d):
             bf.bf_tune_set(variant, d, r, cls, context, rows)
             timings[rows] = _time_ms(run, reps)
     finally:

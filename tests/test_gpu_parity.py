@@ -434,6 +434,82 @@ def test_tc_batch_equals_single_calls_and_oracle(bf, variant):
         _check_tc(got, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
 
 
+def _check_tc_zthr(got, S, Z, s, r, K, u=FP16_U, lowz_frac=0.005):
+    """The near-zero-Z reading's rule for a tensor-core result with channel
+    rounding u: max-abs <= 0.5 (u / 2^-11) where Re Z >= _tc_zthr, the same
+    model's scaled bound below it down to the 1e-2 exclusion, PSNR >=
+    50 - 20 log10(u / 2^-11) dB over all pixels above the exclusion."""
+    scale = u / FP16_U
+    zthr = _tc_zthr(s, r, K)
+    base = Z >= _zmin(s, r)
+    hi = Z >= zthr
+    lo = base & ~hi
+    err = np.abs(got - S).max(axis=0)
+    assert (~base).mean() <= lowz_frac and np.isfinite(got).all()
+    psnr = O.psnr(S[:, base], got[:, base])
+    print(f"tc parity (u = 2^{math.log2(u):.0f}): {hi.mean():.4f} of pixels above zthr {zthr:.2f}, max-abs "
+          f"{err[hi].max():.4f}; {lo.sum()} below it, max-abs {err[lo].max() if lo.any() else 0.0:.4f}; "
+          f"PSNR {psnr:.2f} dB")
+    assert err[hi].max() <= TC_MAXABS * scale
+    if lo.any():
+        assert np.all(err[lo] <= TC_MAXABS * scale * zthr / Z[lo])
+    assert psnr >= TC_PSNR - 20 * math.log10(scale)
+
+
+@pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
+@pytest.mark.parametrize("H,W,s,K,seed", [
+    (256, 256, 3.0, 32, 1),        # several tiles
+    (150, 200, 2.5, 32, 2),        # ragged
+    (97, 301, 10.5, 32, 3),        # r = 31, the general loop's widest lag class
+    (1, 100, 2.0, 32, 4),          # one row
+    (100, 1, 2.0, 32, 5),          # one column
+    (9, 11, 5.0, 32, 6),           # image smaller than the window
+    (20, 33, 0.2, 32, 7),          # r = 0
+    (150, 200, 2.5, 16, 8),        # fewer terms than the configured workloads
+])
+def test_tc_six_channels_against_oracle(bf, variant, H, W, s, K, seed):
+    """Six-channel images on the tensor cores (two 8-channel passes per term,
+    the region as 16-bit codes of a per-image affine map): every pixel vs the
+    oracle under the near-zero-Z rule of _check_tc_zthr (BF16 channels round
+    to 2^-8 instead of FP16's 2^-11, so their bounds scale by 8)."""
+    d = 6
+    C = synth.spd_cond(d, seed=800 + seed, lam_min_range=(30.0 ** 2, 40.0 ** 2), cond=5.0)
+    f = synth.voronoi_image(H, W, d, 6, 10.0, seed=810 + seed)
+    plan = bf.bf_plan(d, C, s, 10, K, 820 + seed)
+    got = _run(bf, plan, f, bf.VARIANTS[variant])
+    ref, res = _oracle_full(f, s, C, 10, K, 820 + seed)
+    _check_tc_zthr(got, res["S"], res["Zre"], s, ref["r"], K, FP16_U if variant == "fp16tc" else 2.0 ** -8)
+
+
+@pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
+def test_tc_mixed_channel_batch_equals_single_calls(bf, variant):
+    """d = 3 and d = 6 images in one bf_filter_batch (a launch per channel
+    count): each equals its single call bit for bit, and so does the
+    allocation-free entry point on the same batch."""
+    specs = [(300, 500, 6, 4.0, 16), (200, 130, 3, 8.0, 16), (129, 257, 6, 8.3, 8), (512, 512, 3, 3.0, 8),
+             (700, 650, 6, 6.0, 8), (64, 64, 6, 10.9, 8)]
+    items, outs, outs2, singles, keep = [], [], [], [], []
+    for i, (H, W, d, s, K) in enumerate(specs):
+        f = synth.voronoi_image(H, W, d, 7, 10.0, seed=850 + i)
+        plan = bf.bf_plan(d, synth.spd_cond(d, seed=860 + i), s, 10, K, 870 + i)
+        x = bf.to_pitched(f)
+        y, y2 = bf.pitched_empty(d, H, W), bf.pitched_empty(d, H, W)
+        items.append((plan, x.data_ptr(), y.data_ptr(), H, W, x.stride(1)))
+        outs.append(y)
+        outs2.append(y2)
+        keep.append((plan, x))
+        singles.append(_run(bf, plan, f, bf.VARIANTS[variant]))
+    sp = torch.cuda.current_stream().cuda_stream
+    bf.bf_filter_batch(items, bf.VARIANTS[variant], sp)
+    bf.bf_filter_batch_noalloc([(p, xp, y2.data_ptr(), H, W, pitch) for (p, xp, _, H, W, pitch), y2
+                                in zip(items, outs2)], bf.VARIANTS[variant], sp)
+    torch.cuda.synchronize()
+    assert bf.bf_last_status(sp) == bf.BF_OK
+    for k, (y, y2, single) in enumerate(zip(outs, outs2, singles)):
+        assert np.array_equal(y.cpu().numpy().astype(np.float64), single), f"image {k}"
+        assert np.array_equal(y2.cpu().numpy().astype(np.float64), single), f"image {k} (no-alloc)"
+
+
 @pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
 def test_tc_batch_same_radius_other_sigma(bf, variant):
     """Images of one window radius but different sigma_s (r = floor(3 sigma_s)

@@ -98,18 +98,23 @@ def test_tuned_batch_is_bit_identical(bf, variant):
         bf.bf_tune_clear()
 
 
-def test_tuned_d6_fp32_is_bit_identical(bf):
+@pytest.mark.parametrize("variant", ["fp32", "fp16tc"])
+def test_tuned_d6_is_bit_identical(bf, variant):
+    """Six channels: the FP32 kernel, and the tensor-core kernel whose region
+    codes use one affine map per image, so the tiling cannot change them."""
+    v = bf.VARIANTS[variant]
     specs = [(150, 190, 4.0, 16), (90, 77, 9.0, 16)]
     items = _images(bf, specs, d=6)
     bf.bf_tune_clear()
-    ref = _run(bf, items, bf.BF_FP32)
+    ref = _run(bf, items, v)
+    alone = [_run(bf, [it], v)[0] for it in items]
     try:
-        for plan, x in items:
-            bf.bf_tune_set(bf.BF_FP32, 6, plan.r, bf.bf_tune_size_class(x.shape[1], x.shape[2]),
-                           bf.BF_TUNE_BATCH, 16)
-        got = _run(bf, items, bf.BF_FP32)
-        for a, b in zip(got, ref):
-            assert np.array_equal(a, b)
+        for rows in (16, 32, 48):
+            for plan, x in items:
+                bf.bf_tune_set(v, 6, plan.r, bf.bf_tune_size_class(x.shape[1], x.shape[2]), bf.BF_TUNE_BATCH, rows)
+            got = _run(bf, items, v)
+            for a, b, c in zip(got, ref, alone):
+                assert np.array_equal(a, b) and np.array_equal(a, c), rows
     finally:
         bf.bf_tune_clear()
 
@@ -124,7 +129,7 @@ def test_tuner_keeps_the_fastest_and_cache_restores_it(bf, tmp_path):
         assert summary["tuned"] == 2 and bf.bf_tune_count() == 2
         for rec in cache.entries.values():
             t = {int(k): v for k, v in rec["timings"].items()}
-            assert sorted(t) == tune.candidates(rec["variant"], rec["r"], rec["H"])
+            assert sorted(t) == tune.candidates(rec["variant"], rec["r"], rec["H"], rec["d"])
             assert rec["rows"] == min(t, key=t.get)
             assert bf.bf_tune_get(rec["variant"], rec["d"], rec["r"], rec["size_class"], rec["context"]) == rec["rows"]
         cache.save()
