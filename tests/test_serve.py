@@ -29,7 +29,9 @@ def _requests(bf, n, seed):
     reqs = []
     for i in range(n):
         H, W = int(rng.integers(40, 300)), int(rng.integers(40, 300))
-        d = 3 if i % 4 else 1  # grayscale requests go through the FP32 kernel in the same batch
+        # grayscale requests go through the FP32 kernel in the same batch, six-channel
+        # ones through the tensor cores' six-channel launch
+        d = (1, 3, 6, 3)[i % 4]
         s = float(rng.uniform(1.0, 6.0))
         sr = float(rng.uniform(20, 60))
         f = synth.voronoi_image(H, W, d, 6, 10.0, seed=seed * 100 + i)
