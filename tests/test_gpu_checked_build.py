@@ -20,7 +20,7 @@ pytestmark = [pytest.mark.gpu,
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
-# (H, W, sigma_s, K, images, variant, entry)
+# (H, W, sigma_s, K, images, variant, entry[, d])
 CASES = [
     (120, 150, 3.0, 8, 1, "fp16tc", "batch"),      # alone: fitted 16-row tile, general loop
     (170, 150, 8.0, 8, 2, "fp16tc", "batch"),      # batch: 80-row tiles, specialised loop (lag 3)
@@ -30,6 +30,9 @@ CASES = [
     (9, 11, 5.0, 4, 1, "bf16tc", "batch"),         # image smaller than the window
     (96, 200, 4.0, 8, 2, "bf16tc", "batch"),       # batch, specialised loop (lag 2)
     (130, 77, 2.5, 8, 3, "fp16tc", "noalloc"),     # allocation-free entry point
+    (100, 140, 4.0, 8, 2, "fp16tc", "batch", 6),   # six channels: 16-bit region codes, two passes per term
+    (9, 11, 10.9, 4, 1, "bf16tc", "batch", 6),     # six channels, r = 32, image smaller than the window
+    (77, 65, 2.0, 4, 2, "fp16tc", "noalloc", 6),   # six channels through the allocation-free entry point
 ]
 
 SCRIPT = textwrap.dedent("""
@@ -38,14 +41,15 @@ SCRIPT = textwrap.dedent("""
     from paper_1605_02164_gb300 import bf, synth
     cases, out = json.loads(sys.argv[1]), sys.argv[2]
     res = {}
-    for i, (H, W, s, K, n, variant, entry) in enumerate(cases):
-        C = synth.spd_cond(3, seed=900 + i)
+    for i, (H, W, s, K, n, variant, entry, *dd) in enumerate(cases):
+        d = dd[0] if dd else 3
+        C = synth.spd_cond(d, seed=900 + i)
         plans, xs, ys = [], [], []
         for j in range(n):
-            f = synth.voronoi_image(H, W, 3, 5, 10.0, seed=910 + 10 * i + j)
-            plans.append(bf.bf_plan(3, C, s, 10, K, 920 + i))
+            f = synth.voronoi_image(H, W, d, 5, 10.0, seed=910 + 10 * i + j)
+            plans.append(bf.bf_plan(d, C, s, 10, K, 920 + i))
             xs.append(bf.to_pitched(f))
-            ys.append(bf.pitched_empty(3, H, W))
+            ys.append(bf.pitched_empty(d, H, W))
         items = [(p, x.data_ptr(), y.data_ptr(), H, W, x.stride(1)) for p, x, y in zip(plans, xs, ys)]
         call = bf.bf_filter_batch if entry == "batch" else bf.bf_filter_batch_noalloc
         call(items, bf.VARIANTS[variant], torch.cuda.current_stream().cuda_stream)

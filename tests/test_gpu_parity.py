@@ -591,19 +591,25 @@ def test_tc_two_term_ring_geometries(bf, s, variant):
     _check_tc(alone, res["S"], res["Zre"], s, ref["r"], lowz_frac=0.005)
 
 
+@pytest.mark.parametrize("d", [3, 6])
 @pytest.mark.parametrize("batch", [False, True])
-def test_tc_bounded_wait_reports_timeout(bf, batch):
+def test_tc_bounded_wait_reports_timeout(bf, batch, d):
     """An injected fault (bf_debug_inject(BF_FAULT_TC_WAIT)) makes the
     tensor-core kernel skip its first MMA group, so the compute warps' bounded
     wait runs out: the launch ends (no hang), its status reads BF_ERR_TIMEOUT,
     and the next call on the same stream is correct again with status BF_OK.
-    Alone, this image runs the general step loop; a batch of two runs the
-    specialised one (r = 9, 80-row tiles)."""
+    Alone, the three-channel image runs the general step loop; a batch of two
+    runs the specialised one (r = 9, 80-row tiles); six-channel images run the
+    six-channel kernel (general loop, two passes per term)."""
     w = synth.WORKLOADS["small"]()
-    f = w.image()[:, :120, :150].copy()
-    plan = bf.bf_plan(w.d, w.C, w.sigma_s, w.N, 8, 31)
+    if d == 3:
+        f = w.image()[:, :120, :150].copy()
+        plan = bf.bf_plan(w.d, w.C, w.sigma_s, w.N, 8, 31)
+    else:
+        f = synth.voronoi_image(120, 150, 6, 5, 10.0, seed=32)
+        plan = bf.bf_plan(6, synth.spd_cond(6, seed=33), w.sigma_s, w.N, 8, 31)
     x = bf.to_pitched(f)
-    ys = [bf.pitched_empty(3, 120, 150) for _ in range(2 if batch else 1)]
+    ys = [bf.pitched_empty(d, 120, 150) for _ in range(2 if batch else 1)]
 
     def launch():
         items = [(plan, x.data_ptr(), y.data_ptr(), 120, 150, x.stride(1)) for y in ys]
