@@ -51,7 +51,7 @@ static_assert(128 * kRegsIssuer + kComputeThreads * kRegsCompute <= kT * kRegsLa
 constexpr int kBX = 64;        // output columns per tile
 constexpr int kNC = 8;         // 16-row chunks per region (128 rows)
 constexpr int kNOC = 5;        // output chunks (of 16 rows) per tile at most
-constexpr int kNOC6 = 3;       // the same for six-channel images
+constexpr int kNOC6 = 4;       // the same for six-channel images
 constexpr uint32_t kColF = 0;  // TMEM columns: region f (384), D1 (64), D2 (64)
 constexpr uint32_t kColD1 = 384;
 constexpr uint32_t kColD2 = 448;
@@ -335,7 +335,7 @@ __device__ __forceinline__ uint32_t bits(T v) {
 // sin f_1..f_4; then cos f_5, cos f_6, cos, 0 and sin f_5, sin f_6, sin, 0);
 // the region is held as 16-bit codes of a per-tile, per-channel affine map
 // (6 channels x 128 columns fit the same 384 TMEM columns), tiles are at most
-// 48 rows (two sets of accumulators), and every tile runs the general loop.
+// 64 rows (two sets of accumulators), and every tile runs the general loop.
 template <bool BF16, int FIX, bool D6>
 __global__ void __launch_bounds__(kT, 1)
     mcsf_tc_kernel(const TcImg *__restrict__ imgs, int n_imgs, int total_tiles, int *__restrict__ ctrl,

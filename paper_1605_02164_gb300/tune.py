@@ -41,7 +41,7 @@ def tc_max_rows(r: int) -> int:
 def candidates(variant: int, r: int, H: int, d: int = 3) -> list[int]:
     top = tc_max_rows(r) if variant in (bf.BF_FP16TC, bf.BF_BF16TC) else 128
     if variant in (bf.BF_FP16TC, bf.BF_BF16TC) and d == 6:
-        top = min(top, 48)  # two sets of accumulators: at most 3 output chunks
+        top = min(top, 64)  # two sets of accumulators: at most 4 output chunks
     top = min(top, 16 * (-(-H // 16)))  # no taller than the image needs
     return list(range(16, top + 1, 16))
 

@@ -172,7 +172,7 @@ def test_tune_cache_round_trip(lib, tmp_path):
         assert tune.candidates(bf.BF_FP16TC, 24, 2160) == [16, 32, 48, 64, 80]
         assert tune.candidates(bf.BF_FP16TC, 32, 2160) == [16, 32, 48, 64]
         assert tune.candidates(bf.BF_FP32, 3, 40) == [16, 32, 48]
-        assert tune.candidates(bf.BF_FP16TC, 24, 2160, 6) == [16, 32, 48]
+        assert tune.candidates(bf.BF_FP16TC, 24, 2160, 6) == [16, 32, 48, 64]
     finally:
         bf.bf_tune_clear()
 
