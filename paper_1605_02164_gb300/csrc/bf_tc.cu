@@ -70,14 +70,18 @@ __host__ __device__ constexpr int ring_xor(int t) { return (t & 3) | ((t & 4) <<
 // TcImg::spec lists the same values): the default tile of the lag classes
 // r = 1..8, 9..16 and 17..24; the 32-row tiles a 512 x 512 image takes alone at
 // r = 1..8 and 9..16 (two-term centre ring); the 64-row tile of a 1024 x 1024
-// image alone at r = 9..16.  (r = 25..32 keeps the general loop: a 128-row
-// centre ring would take the shared memory past 227 KB.)
-constexpr int kNumSpec = 6;
+// image alone at r = 9..16; for six-channel images, whose tiles are at most
+// 64 rows, also the 64-row tiles of r = 1..8, 17..24 and 25..32 (dmask: bit 0
+// three-channel, bit 1 six-channel images).  (A three-channel tile of r =
+// 25..32 keeps the general loop: its 128-row centre ring would take the
+// shared memory past 227 KB.)
+constexpr int kNumSpec = 9;
 struct SpecGeom {
-    int nc, lag, BY, terms;
+    int nc, lag, BY, terms, dmask;
 };
-constexpr SpecGeom kSpecGeom[kNumSpec] = {{6, 1, 80, 1}, {7, 2, 80, 1}, {8, 3, 80, 1},
-                                          {3, 1, 32, 2}, {4, 2, 32, 2}, {6, 2, 64, 1}};
+constexpr SpecGeom kSpecGeom[kNumSpec] = {{6, 1, 80, 1, 1}, {7, 2, 80, 1, 1}, {8, 3, 80, 1, 1},
+                                          {3, 1, 32, 2, 3}, {4, 2, 32, 2, 3}, {6, 2, 64, 1, 3},
+                                          {5, 1, 64, 1, 2}, {7, 3, 64, 1, 2}, {8, 4, 64, 1, 2}};
 template <int V>
 using IC = std::integral_constant<int, V>;
 
@@ -926,17 +930,27 @@ __global__ void __launch_bounds__(kT, 1)
                 static_assert(NOBT <= NOC, "geometry");
                 constexpr bool kParConst = NCT % 2 == 0, kRingConst = NCT % (LAGT + 1) == 0;
                 auto tbase = [&](int kk) { return PT == 2 ? (kk & 1) * 16 * NCT : 0; };
+                // A six-channel tile runs 2K passes as the "terms" k of the loop
+                // (pass k & 1 of term k >> 1).
                 int krS = 0;  // 16 s mod Kw when it is not a constant
-                for (int k = 0; k < K; ++k) {
+                for (int k = 0; k < KP; ++k) {
                     const int kpar = kParConst ? 0 : (k & 1);
                     const int tb = tbase(k);
     #pragma unroll
                     for (int c = 0; c < NCT; ++c) {
                         if (c + 1 < NCT) {
-                            stage_A(kpar + c + 1, c + 1, tb + 16 * (c + 1));
-                        } else if (k + 1 < K) {
-                            load_nu(k + 1);
-                            stage_A(kParConst ? 0 : (k + 1) & 1, 0, tbase(k + 1));
+                            if constexpr (D6)
+                                stage_A6(kpar + c + 1, c + 1, tb + 16 * (c + 1), k & 1);
+                            else
+                                stage_A(kpar + c + 1, c + 1, tb + 16 * (c + 1));
+                        } else if (k + 1 < KP) {
+                            if constexpr (D6) {
+                                if (((k + 1) & 1) == 0) load_nu((k + 1) >> 1);
+                                stage_A6(kParConst ? 0 : (k + 1) & 1, 0, tbase(k + 1), (k + 1) & 1);
+                            } else {
+                                load_nu(k + 1);
+                                stage_A(kParConst ? 0 : (k + 1) & 1, 0, tbase(k + 1));
+                            }
                         }
                         // output chunk completed by the previous step (of term k - 1 when c = 0)
                         const int ocp = (c == 0 ? NCT - 1 : c - 1) - LAGT;
@@ -944,7 +958,7 @@ __global__ void __launch_bounds__(kT, 1)
                             if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                             ph2 ^= 1;
                             fence_after();
-                            stage_C(ocp, (c == 0 ? tbase(k - 1) : tb) + 16 * ocp + 8 * e);
+                            stage_C(ocp, (c == 0 ? tbase(k - 1) : tb) + 16 * ocp + 8 * e, (c == 0 ? k - 1 : k) & 1);
                         }
                         if (!mbar_wait(&mbar[0], ph1, lay.spin)) timed_out = true;
                         ph1 ^= 1;
@@ -963,7 +977,7 @@ __global__ void __launch_bounds__(kT, 1)
                     if (!mbar_wait(&mbar[1], ph2, lay.spin)) timed_out = true;
                     ph2 ^= 1;
                     fence_after();
-                    stage_C(NCT - 1 - LAGT, tbase(K - 1) + 16 * (NCT - 1 - LAGT) + 8 * e);
+                    stage_C(NCT - 1 - LAGT, tbase(KP - 1) + 16 * (NCT - 1 - LAGT) + 8 * e, (KP - 1) & 1);
                 }
                 return true;
             };
@@ -1033,8 +1047,17 @@ __global__ void __launch_bounds__(kT, 1)
                 return true;
             };
             bool go;
-            if constexpr (D6) go = general_loop();
-            else switch (FIX ? FIX : g.spec) {
+            if constexpr (D6) {
+                switch (g.spec) {  // the entries of kSpecGeom whose dmask has bit 1
+                    case 4: go = spec_loop(IC<3>(), IC<1>(), IC<2>(), IC<2>()); break;
+                    case 5: go = spec_loop(IC<4>(), IC<2>(), IC<2>(), IC<2>()); break;
+                    case 6: go = spec_loop(IC<6>(), IC<2>(), IC<4>(), IC<1>()); break;
+                    case 7: go = spec_loop(IC<5>(), IC<1>(), IC<4>(), IC<1>()); break;
+                    case 8: go = spec_loop(IC<7>(), IC<3>(), IC<4>(), IC<1>()); break;
+                    case 9: go = spec_loop(IC<8>(), IC<4>(), IC<4>(), IC<1>()); break;
+                    default: go = general_loop(); break;
+                }
+            } else switch (FIX ? FIX : g.spec) {
                 case 1: go = spec_loop(IC<6>(), IC<1>(), IC<5>(), IC<1>()); break;
                 case 2: go = spec_loop(IC<7>(), IC<2>(), IC<5>(), IC<1>()); break;
                 case 3: go = spec_loop(IC<8>(), IC<3>(), IC<5>(), IC<1>()); break;
@@ -1281,7 +1304,8 @@ void tc_finish(TcImg *tab, int m, int *total, TcLayout *lay) {
     const long long ring_rows = ((long long)max_smem - 1024 - (long long)base.offC) / (kBX * 8);
     for (int i = 0; i < m; ++i) {
         tab[i].spec = 0;
-        for (int j = 0; j < kNumSpec && tab[i].d == 3; ++j) {
+        for (int j = 0; j < kNumSpec; ++j) {
+            if (!((kSpecGeom[j].dmask >> (tab[i].d == 6 ? 1 : 0)) & 1)) continue;
             const int rows = 16 * kSpecGeom[j].nc * kSpecGeom[j].terms;
             if (tab[i].nc == kSpecGeom[j].nc && tab[i].lag == kSpecGeom[j].lag && tab[i].BY == kSpecGeom[j].BY &&
                 rows <= ring_rows) {

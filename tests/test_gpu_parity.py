@@ -568,6 +568,37 @@ def test_tc_specialised_geometries(bf, s, variant):
 
 
 @pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
+@pytest.mark.parametrize("s", [2.0, 4.0, 7.0, 10.0])
+def test_tc_six_channel_specialised_geometries(bf, s, variant):
+    """Six-channel batches keep 64-row tiles, so two images of one sigma_s run
+    the step loop specialised to (chunks, lag) = (5, 1), (6, 2), (7, 3) or
+    (8, 4) for r = 6, 12, 21, 30, with the two passes per term as its terms.
+    Each result equals filtering the image alone (a shorter tile and the
+    general loop for these sizes) and meets the near-zero-Z rule against the
+    oracle."""
+    items, outs, keep, singles, refs = [], [], [], [], []
+    for i, (H, W) in enumerate([(150, 170), (100, 200)]):
+        C = synth.spd_cond(6, seed=830 + i, lam_min_range=(30.0 ** 2, 40.0 ** 2), cond=5.0)
+        f = synth.voronoi_image(H, W, 6, 7, 10.0, seed=840 + i)
+        plan = bf.bf_plan(6, C, s, 10, 32, 95 + i)
+        x = bf.to_pitched(f)
+        y = bf.pitched_empty(6, H, W)
+        items.append((plan, x.data_ptr(), y.data_ptr(), H, W, x.stride(1)))
+        outs.append(y)
+        keep.append((x, plan))
+        singles.append(_run(bf, plan, f, bf.VARIANTS[variant]))
+        refs.append((f, C, 95 + i))
+    bf.bf_filter_batch(items, bf.VARIANTS[variant], torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert bf.bf_last_status(0) == bf.BF_OK
+    for y, single, (f, C, seed) in zip(outs, singles, refs):
+        got = y.cpu().numpy().astype(np.float64)
+        assert np.array_equal(got, single)
+        ref, res = _oracle_full(f, s, C, 10, 32, seed)
+        _check_tc_zthr(got, res["S"], res["Zre"], s, ref["r"], 32, FP16_U if variant == "fp16tc" else 2.0 ** -8)
+
+
+@pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
 @pytest.mark.parametrize("s", [1.0, 4.0])
 def test_tc_two_term_ring_geometries(bf, s, variant):
     """A 512x512 image alone takes 32-row tiles (one wave of 128 tiles), which
