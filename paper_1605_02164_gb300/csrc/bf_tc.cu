@@ -1449,8 +1449,9 @@ int tc_launch_batch(const bf_item *items, int n, int variant, void *scratch, int
 // ---------------------------------------------------------------------------------
 
 // Scratch of bf_filter_batch_noalloc: control words (tile counter, status)
-// followed by the image table for at most BF_NOALLOC_MAX_ITEMS images.  Every
-// GPU that loads the library holds these 26.25 KB until the process exits.
+// followed by the image table and the six-channel range keys (12 words per
+// image) for at most BF_NOALLOC_MAX_ITEMS images.  Every
+// GPU that loads the library holds these 40.25 KB until the process exits.
 constexpr size_t kNoAllocBytes =
     (size_t)kCtrlWords * sizeof(int) + (size_t)BF_NOALLOC_MAX_ITEMS * (sizeof(TcImg) + 12 * sizeof(uint32_t));
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
