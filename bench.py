@@ -45,8 +45,8 @@ def algorithmic_flops_per_pixel(d: int, r: int, K: int) -> float:
 # only stands for the kernel source it was taken on (sha1 of that file): after
 # any change to the source the bench reports null until a new capture.
 MEASURED_TRAFFIC = {
-    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "df0f1b986352b00550125e3404b0be8f23565ada",
-               "workload": "4k", "bytes_per_launch": 100.645e6 + 59.880e6,
+    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "6c0903765249b2ae19c87fa7cc9ff548d1e8923b",
+               "workload": "4k", "bytes_per_launch": 100.706e6 + 59.710e6,
                "capture": "ncu --set full --clock-control none -k regex:mcsf_tc -s 2 -c 1, one launch of "
                           "bench.py --steps 2 --warmup 3 --variant fp16tc --no-cpu-baseline --no-fp32-compare "
                           "--no-extras --tune off"},
