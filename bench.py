@@ -438,7 +438,9 @@ def setup_tuning(args, groups):
         pass
     return {"mode": "measured (tune.py)", "cache": cache.path, "keys_timed_now": timed,
             "entries": len(cache.entries), "tuning_seconds": round(secs, 2),
-            "key": "variant:d:ceil(r/8):size class:context (0 alone, 1 batch)", "tile_rows": chosen}
+            "key": "variant:d:ceil(r/8):size class:context (0 alone, 1 batch)",
+            "rule": "a measured height replaces the cost model only if it is > 1 % faster (tile_rows 0: the model)",
+            "tile_rows": chosen}
 
 
 def _on_tc(bf, d, variant):
@@ -505,7 +507,7 @@ def batch_line(args):
         keys.append((v, d, it[0].r, w.H, w.W, bf.BF_TUNE_BATCH))
     bf.bf_tune_clear()
     ms_untuned = timed(batched, args.steps)       # the kernels' cost models (tallest tiles)
-    tuning = setup_tuning(args, [(keys, 4)])
+    tuning = setup_tuning(args, [(keys, 32)])  # K = 32, the smallest K of the batch
     ms_batch = timed(batched, args.steps)
     ms_single = timed(lambda: per_image(variant), max(1, args.steps // 2))
     ms_fp32 = timed(lambda: per_image(bf.BF_FP32), 1)
@@ -573,7 +575,7 @@ def serve_line(args):
         for ctx in (bf.BF_TUNE_ALONE, bf.BF_TUNE_BATCH):
             keys.setdefault((v, (r + 7) // 8, bf.bf_tune_size_class(w.H, w.W), ctx),
                             (v, 3, r, w.H, w.W, ctx))
-    tuning = setup_tuning(args, [(list(keys.values()), 8)]) if keys else {"mode": "not tunable"}
+    tuning = setup_tuning(args, [(list(keys.values()), 32)]) if keys else {"mode": "not tunable"}
     if "tile_rows" in tuning:
         tuning["tile_rows"] = len(tuning["tile_rows"])
     srv = Server(budget_bytes=40 << 30, streams=3, max_batch=64, variant=variant,

@@ -71,12 +71,16 @@ def _time_ms(fn, reps: int) -> float:
 
 
 def tune(variant: int, d: int, r: int, H: int, W: int, context: int = bf.BF_TUNE_ALONE, K: int = 16,
-         reps: int = 5, copies: int | None = None, batch_pixels: float = 8e6, seed: int = 7) -> dict:
-    """Measure every candidate tile height for the key and keep the fastest in
-    the library's table.  The batch context is timed on one bf_filter_batch
-    over `copies` copies of the image (default: enough for about
-    `batch_pixels` pixels, 2 to 64 copies), so that the SMs see several waves
-    of tiles as in a real batch.  Returns {"rows", "ms", "timings", ...}."""
+         reps: int = 5, copies: int | None = None, batch_pixels: float = 8e6, seed: int = 7,
+         margin: float = 0.01) -> dict:
+    """Measure every candidate tile height for the key, and the cost model's
+    own choice (no entry, timed as rows 0); keep a height in the library's
+    table only if it beats the cost model by more than `margin` (else no
+    entry: the model stays).  The batch context is timed on one
+    bf_filter_batch over `copies` copies of the image (default: enough for
+    about `batch_pixels` pixels, 2 to 64 copies), so that the SMs see several
+    waves of tiles as in a real batch.  Returns {"rows", "ms", "timings", ...}
+    (rows 0: the cost model)."""
     import torch
     cls = bf.bf_tune_size_class(H, W)
     C = np.diag([40.0 ** 2] * d)
@@ -102,12 +106,14 @@ def tune(variant: int, d: int, r: int, H: int, W: int, context: int = bf.BF_TUNE
     prev = bf.bf_tune_get(variant, d, r, cls, context)
     timings = {}
     try:
-        for rows in candidates(variant, r, H, d):
+        for rows in [0] + candidates(variant, r, H, d):  # 0: no entry, the cost model
             bf.bf_tune_set(variant, d, r, cls, context, rows)
             timings[rows] = _time_ms(run, reps)
     finally:
         bf.bf_tune_set(variant, d, r, cls, context, prev)
     best = min(timings, key=timings.get)
+    if best != 0 and timings[best] > (1.0 - margin) * timings[0]:
+        best = 0  # within the margin of the cost model's choice: keep the model
     bf.bf_tune_set(variant, d, r, cls, context, best)
     if bf.bf_last_status(sp) != bf.BF_OK:
         raise RuntimeError("device status after tuning")

@@ -126,17 +126,21 @@ def test_tuner_keeps_the_fastest_and_cache_restores_it(bf, tmp_path):
         cache = tune.TuneCache(str(tmp_path / "t.json"))
         keys = [(bf.BF_FP16TC, 3, 9, 700, 1000, bf.BF_TUNE_ALONE), (bf.BF_FP32, 3, 6, 700, 1000, bf.BF_TUNE_BATCH)]
         summary = cache.ensure(keys, K=8, reps=3, copies=2)
-        assert summary["tuned"] == 2 and bf.bf_tune_count() == 2
+        assert summary["tuned"] == 2 and len(cache.entries) == 2
+        assert bf.bf_tune_count() == sum(rec["rows"] > 0 for rec in cache.entries.values())
         for rec in cache.entries.values():
             t = {int(k): v for k, v in rec["timings"].items()}
-            assert sorted(t) == tune.candidates(rec["variant"], rec["r"], rec["H"], rec["d"])
-            assert rec["rows"] == min(t, key=t.get)
+            assert sorted(t) == [0] + tune.candidates(rec["variant"], rec["r"], rec["H"], rec["d"])
+            best = min(t, key=t.get)
+            if best != 0 and t[best] > 0.99 * t[0]:
+                best = 0  # a measured height must beat the cost model (rows 0) by 1 %
+            assert rec["rows"] == best
             assert bf.bf_tune_get(rec["variant"], rec["d"], rec["r"], rec["size_class"], rec["context"]) == rec["rows"]
         cache.save()
         assert cache.ensure(keys)["tuned"] == 0        # nothing new to time
         bf.bf_tune_clear()
         again = tune.TuneCache(cache.path)
-        assert again.apply() == 2
+        assert again.apply() == 2 and bf.bf_tune_count() == sum(r["rows"] > 0 for r in cache.entries.values())
         for rec in cache.entries.values():
             assert bf.bf_tune_get(rec["variant"], rec["d"], rec["r"], rec["size_class"], rec["context"]) == rec["rows"]
     finally:
