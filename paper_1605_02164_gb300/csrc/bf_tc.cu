@@ -1180,7 +1180,8 @@ namespace {
 // the block takes, then one atomic per warp.  The keys start at 0xFFFFFFFF
 // (minima) and 0 (maxima).
 __global__ void __launch_bounds__(256) tc_range_kernel(const TcImg *__restrict__ imgs, int m) {
-    const TcImg &g = imgs[blockIdx.y];
+  for (int im = blockIdx.y; im < m; im += gridDim.y) {  // grid.y is capped at 65535 images
+    const TcImg &g = imgs[im];
     const size_t plane = (size_t)g.H * g.pitch;
     float mn[6], mx[6];
 #pragma unroll
@@ -1211,6 +1212,7 @@ __global__ void __launch_bounds__(256) tc_range_kernel(const TcImg *__restrict__
             atomicMax(g.mm + 6 * m + ch, order_key(mx[ch]));
         }
     }
+  }
 }
 
 // Range keys of a six-channel table at `keys` (6 m minima, then 6 m maxima):
@@ -1221,7 +1223,7 @@ int tc_ranges(const TcImg *imgs_dev, uint32_t *keys, int m, cudaStream_t s) {
         cudaGetLastError();
         return BF_ERR_CUDA;
     }
-    tc_range_kernel<<<dim3(64, m), 256, 0, s>>>(imgs_dev, m);
+    tc_range_kernel<<<dim3(64, std::min(m, 65535)), 256, 0, s>>>(imgs_dev, m);
     return cuda_err(cudaGetLastError());
 }
 
