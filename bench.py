@@ -45,8 +45,8 @@ def algorithmic_flops_per_pixel(d: int, r: int, K: int) -> float:
 # only stands for the kernel source it was taken on (sha1 of that file): after
 # any change to the source the bench reports null until a new capture.
 MEASURED_TRAFFIC = {
-    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "6c0903765249b2ae19c87fa7cc9ff548d1e8923b",
-               "workload": "4k", "bytes_per_launch": 100.706e6 + 59.710e6,
+    "fp16tc": {"src": "paper_1605_02164_gb300/csrc/bf_tc.cu", "sha1": "b8fa87f89fe4eb04a64620dc9037a1326a0b8139",
+               "workload": "4k", "bytes_per_launch": 100.143e6 + 60.060e6,
                "capture": "ncu --set full --clock-control none -k regex:mcsf_tc -s 2 -c 1, one launch of "
                           "bench.py --steps 2 --warmup 3 --variant fp16tc --no-cpu-baseline --no-fp32-compare "
                           "--no-extras --tune off"},
