@@ -481,6 +481,29 @@ def test_tc_six_channels_against_oracle(bf, variant, H, W, s, K, seed):
     _check_tc_zthr(got, res["S"], res["Zre"], s, ref["r"], K, FP16_U if variant == "fp16tc" else 2.0 ** -8)
 
 
+@pytest.mark.parametrize("case", ["constant_channel", "negative_values"])
+def test_tc_six_channel_code_ranges(bf, case):
+    """The 16-bit region codes map each channel's own range: a constant
+    channel (zero range, scale 0: decoded exactly) and values far from
+    0..255 (here -300..-100 and 0..20) meet the near-zero-Z rule against the
+    oracle like any other six-channel image."""
+    H, W, s, K = 90, 140, 3.0, 32
+    f = synth.voronoi_image(H, W, 6, 6, 10.0, seed=870).astype(np.float64)
+    if case == "constant_channel":
+        f[4] = 77.25
+    else:
+        f[0] = -300.0 + 200.0 * f[0] / 255.0
+        f[3] = 20.0 * f[3] / 255.0
+    f = f.astype(np.float32)
+    C = synth.spd_cond(6, seed=871, lam_min_range=(30.0 ** 2, 40.0 ** 2), cond=5.0)
+    plan = bf.bf_plan(6, C, s, 10, K, 872)
+    got = _run(bf, plan, f, bf.BF_FP16TC)
+    ref, res = _oracle_full(f, s, C, 10, K, 872)
+    if case == "constant_channel":
+        assert np.abs(got[4] - 77.25).max() <= 1e-3 * 77.25  # a weighted mean of a constant
+    _check_tc_zthr(got, res["S"], res["Zre"], s, ref["r"], K)
+
+
 @pytest.mark.parametrize("variant", ["fp16tc", "bf16tc"])
 def test_tc_mixed_channel_batch_equals_single_calls(bf, variant):
     """d = 3 and d = 6 images in one bf_filter_batch (a launch per channel
